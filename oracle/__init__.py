@@ -1,0 +1,17 @@
+"""FP64 CPU oracle of the SparseOIT renderer.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by the smoke check and by
+the CPU-baseline leg of ``bench.py``.  The product library neither imports
+nor links anything here.
+"""
+from .core import (  # noqa: F401
+    NPARAM,
+    build,
+    backward,
+    compose,
+    num_threads,
+    project,
+    render,
+    render_sums,
+    sh_basis,
+)
