@@ -179,6 +179,29 @@ def test_two_splats_weighted_average():
     assert np.allclose(img2, img, atol=1e-15, rtol=0)
 
 
+def test_view_direction_from_off_origin_camera():
+    """Eq. 4: the SH argument is the unit vector from the camera centre to the mean.
+    Camera on the sphere looking at a splat at the origin: n = the camera's forward axis."""
+    pos = np.array([1.2, -2.5, 2.9])
+    fwd = -pos / np.linalg.norm(pos)
+    right = np.cross(fwd, [0.0, 0.0, 1.0]); right /= np.linalg.norm(right)
+    down = np.cross(fwd, right)
+    R = np.stack([right, down, fwd])
+    cam = dict(R=R, t=-R @ pos, fx=80.0, fy=80.0, cx=8.5, cy=8.5, width=17, height=17)
+    sh = np.zeros((16, 3))
+    sh[0] = [0.1, 0.0, 0.2]
+    sh[1] = [0.3, -0.2, 0.1]   # l=1, m=-1 (y)
+    sh[2] = [-0.1, 0.25, 0.0]  # l=1, m=0  (z)
+    sh[3] = [0.2, 0.1, -0.3]   # l=1, m=1  (x)
+    o = 0.8
+    sc = make_scene([[0.0, 0.0, 0.0]], [[-2.0] * 3], [logit(o)], sh_color=[sh], sigma=9.0, bg=(0.0, 0.0, 0.0))
+    img = oracle.render(sc, cam)["image"][8, 8]
+    n = fwd
+    k1 = math.sqrt(3.0 / (4.0 * math.pi))
+    c = 0.5 + sh[0] * _zonal(0) + k1 * (n[1] * sh[1] + n[2] * sh[2] + n[0] * sh[3])
+    assert np.allclose(img, o * c, atol=1e-14, rtol=0)
+
+
 def test_far_splat_attenuates_only():
     """A splat beyond sigma has w = 0: Q = 0, F := 0 and C = T c0 (Eq. 1, 7)."""
     cam = axis_camera(9, 9, f=50.0)
@@ -279,12 +302,15 @@ def _loss(sc, cam, g):
     return float(np.sum(oracle.render(sc, cam)["image"] * g))
 
 
-@pytest.mark.parametrize("seed", [21, 22])
-def test_gradient_matches_central_finite_differences(seed):
+@pytest.mark.parametrize("seed,opacity_shift", [(21, 0.0), (22, 0.0), (23, 9.0)])
+def test_gradient_matches_central_finite_differences(seed, opacity_shift):
     sc = small_random_scene(40, seed, log_scale_mean=-2.0)
+    sc["opacity_logits"] = sc["opacity_logits"] + opacity_shift  # shift 9: pairs clamped at 0.99
     for k in ("means", "quats", "log_scales", "opacity_logits", "sh_color", "sh_weight"):
         sc[k] = sc[k].copy()
-    cam = front_camera(32, 28)
+    # with the shift, a narrow field of view makes splats ~6 px wide so that the
+    # clamped core (p < ln(1/0.99), radius 0.14 sigma') covers whole pixels
+    cam = front_camera(32, 28, fov_deg=12.0 if opacity_shift > 0 else 50.0)
     r = oracle.render(sc, cam)
     g = np.random.default_rng(seed).normal(size=r["image"].shape)
     grads, dsig, amb = oracle.backward(sc, cam, r["sums"], g, amb_band=1e-3)
@@ -306,6 +332,8 @@ def test_gradient_matches_central_finite_differences(seed):
             assert abs(fd - grads[i, j]) <= 2e-6 * scale + 1e-7, (i, j, fd, grads[i, j])
             checked += 1
     assert checked > 200
+    if opacity_shift > 0:
+        assert r["clamped"] > 20
     # sigma (Eq. 1): every splat's weight depends on it
     proj = oracle.project(sc, cam)
     if np.all(np.abs(proj[proj[:, 0] == 1, 21]) > 1e-3):
