@@ -1,0 +1,217 @@
+/*
+ * sparseoit.h -- C ABI of libsparseoit, the GB300 (sm_103a) implementation
+ * of SparseOIT's differentiable order-independent-transparency Gaussian
+ * splat renderer restricted to an active set of splats (arXiv 2605.13855).
+ *
+ * What is computed (paper references are to sections / equations /
+ * algorithms of the paper):
+ *   - Eq. 7 (weighted-blended OIT):  C = T c0 + (1 - T) P / Q,
+ *       P = sum_i c_i a_i w_i,  Q = sum_i a_i w_i,  T = prod_i (1 - a_i),
+ *     with the per-pixel opacity a_i of Eq. 5, the 2D covariance of Eq. 6
+ *     (from Sigma = R S S^T R^T, Eq. 2), the degree-3 SH colour of Eq. 4 and
+ *     the OIT weight w = max(0, 1 - d/sigma) v(r) of Eq. 1.
+ *   - Sec. 4.1 (active set): only splats in the active set A are projected,
+ *     binned and accumulated each iteration; the frozen complement's
+ *     per-pixel sums (P, Q, log T) sit in device buffers, one per training
+ *     view, and are combined with A's sums (P = P_A + P_F, Q = Q_A + Q_F,
+ *     T = T_A exp(logT_F)).  Their update after an active-set change is
+ *     delayed until the view is used (Sec. 4.1 "Implementation Details",
+ *     Alg. 2 "BAU").
+ *   - App. A / Alg. 2: binning by tile id only (no depth sort).
+ *   - App. B / Eq. 9-10 and Sec. 4.2: backward pass; only A's parameters
+ *     receive gradients.
+ *
+ * Conventions shared by every call:
+ *   - Every function returns 0 (SPARSEOIT_OK) or a negative error code and
+ *     never throws or aborts; sparseoit_last_error() then describes it.
+ *   - `stream` is a cudaStream_t (passed as void* so this header needs no
+ *     CUDA include).  Work is enqueued on it and the call returns without
+ *     waiting, except where a call says it synchronises.
+ *   - Pointers documented "device" must be device (or managed) memory that
+ *     the caller owns and keeps alive until the enqueued work completes.
+ *     "host" pointers are read before the call returns.
+ *   - Arrays are dense, row-major, 32-bit float unless stated.
+ *   - Pixel (x, y) of a W x H view has its centre at (x + 0.5, y + 0.5);
+ *     images are [H, W, 3] (HWC).
+ *   - The context owns its workspace (projected records, tile bins, pixel
+ *     states, frozen sums); it is allocated with cudaMalloc on the current
+ *     device in sparseoit_create / sparseoit_set_active and grown there when
+ *     needed.  One context must not be used from two host threads at once.
+ */
+#ifndef SPARSEOIT_H
+#define SPARSEOIT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPARSEOIT_ABI_VERSION 1
+#define SPARSEOIT_MAX_BATCH_VIEWS 32   /* views in one forward / backward call */
+
+/* Error codes. */
+enum {
+    SPARSEOIT_OK = 0,
+    SPARSEOIT_ERR_INVALID_ARG = -1,  /* a null / out-of-range argument            */
+    SPARSEOIT_ERR_OOM = -2,          /* cudaMalloc failed                          */
+    SPARSEOIT_ERR_CUDA = -3,         /* a CUDA runtime call or launch failed       */
+    SPARSEOIT_ERR_STATE = -4,        /* call out of order: forward on a view whose
+                                        frozen sums are stale, backward without a
+                                        forward, forward before set_active         */
+    SPARSEOIT_ERR_CAPACITY = -5,     /* the (splat, tile) pair arena overflowed;
+                                        outputs of that call are invalid; enlarge
+                                        it with sparseoit_reserve_pairs and redo   */
+    SPARSEOIT_ERR_TIMEOUT = -6       /* a bounded device-side wait gave up         */
+};
+
+/* Storage type of the SH coefficient arrays. */
+enum { SPARSEOIT_F32 = 0, SPARSEOIT_BF16 = 1 };
+
+/* Frozen-sum update modes (sparseoit_commit_frozen). */
+enum {
+    SPARSEOIT_COMMIT_INCREMENTAL = 0, /* add D+ = A_old \ A_new, subtract D- = A_new \ A_old */
+    SPARSEOIT_COMMIT_RECOMPUTE = 1    /* re-render the whole complement of A                */
+};
+
+typedef struct sparseoit_ctx sparseoit_ctx;
+
+/* Pinhole camera.  A world point X maps to the camera-space point
+ * t_c = R X + t (x right, y down, z forward) and to the pixel
+ * (fx t_c.x / t_c.z + cx, fy t_c.y / t_c.z + cy).  Splats with t_c.z <= 0.2
+ * are culled.  width / height must equal the view's size given at create. */
+typedef struct {
+    float R[9];          /* world -> camera rotation, row-major */
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} sparseoit_camera;
+
+/* The full splat set G (Sec. 3.1 / 3.2), device pointers, n rows each. */
+typedef struct {
+    const float *means;           /* [n, 3] centre mu                                 */
+    const float *quats;           /* [n, 4] rotation quaternion (w, x, y, z), any norm */
+    const float *log_scales;      /* [n, 3] log of the axis scales s                  */
+    const float *opacity_logits;  /* [n]    opacity o = sigmoid(logit)                */
+    const void *sh_color;         /* [n, 16, 3] colour SH h (degree 3), sh_dtype      */
+    const void *sh_weight;        /* [n, 16] OIT-weight SH v (single channel)         */
+    int32_t sh_dtype;             /* SPARSEOIT_F32 or SPARSEOIT_BF16                  */
+    float sigma;                  /* scene depth scale of Eq. 1 (> 0)                 */
+    float bg[3];                  /* background colour c0 of Eq. 7                    */
+    int64_t n;                    /* number of splats (== max_splats of the context)  */
+} sparseoit_splats;
+
+/* Gradient outputs, device pointers.  Only active splats receive gradients
+ * (Sec. 4.1).  With rows_by_splat == 0 the rows are COMPACT: row r belongs to
+ * the r-th active splat in ascending splat index (sparseoit_get_active) and
+ * the arrays have n_active rows.  With rows_by_splat != 0 the arrays have n
+ * rows, an active splat's gradient goes to the row of its splat index and
+ * the rows of inactive splats are not written.  FP32 regardless of sh_dtype;
+ * quats, sh_color and sh_weight 16-byte aligned.  The active rows (and
+ * *sigma) are overwritten by sparseoit_backward. */
+typedef struct {
+    float *means;           /* [n_active, 3]     */
+    float *quats;           /* [n_active, 4]     */
+    float *log_scales;      /* [n_active, 3]     */
+    float *opacity_logits;  /* [n_active]        */
+    float *sh_color;        /* [n_active, 16, 3] */
+    float *sh_weight;       /* [n_active, 16]    */
+    float *sigma;           /* [1]: dL/dsigma summed over active splats and views */
+    int32_t rows_by_splat;  /* 0: compact rows, else rows indexed by splat index */
+} sparseoit_grads;
+
+/* Launch configuration (NULL = defaults). */
+typedef struct {
+    int64_t max_pairs;      /* capacity of the (splat, tile) pair arena shared by
+                               the views of one call; 0 = 1 << 25               */
+    int32_t bwd_splats_per_warp; /* reserved, 0 = default (32)                */
+    int32_t reserved[5];
+} sparseoit_config;
+
+/* Create a context for a scene of max_splats splats and n_views training
+ * views of sizes view_w[k] x view_h[k] (host arrays, 1 <= n_views).
+ * Allocates the per-view frozen sums (5 floats per pixel: P_r, P_g, P_b, Q,
+ * log T) and the pixel states.  *out receives the context. */
+int sparseoit_create(sparseoit_ctx **out, int64_t max_splats, int32_t n_views, const int32_t *view_w,
+                     const int32_t *view_h, const sparseoit_config *cfg);
+
+/* Release every buffer of the context (synchronises the device). */
+int sparseoit_destroy(sparseoit_ctx *ctx);
+
+/* Sec. 4.1: set the active set A from a device mask d_mask[n] (nonzero =
+ * active; n == max_splats).  Compacts the mask into the ascending active
+ * index list and records the deltas D+ = A_old \ A_new and D- = A_new \ A_old
+ * against the previous mask for the delayed frozen-sum update.  Every view
+ * becomes stale until sparseoit_commit_frozen.  SYNCHRONISES `stream` (the
+ * host needs |A| to size later launches). */
+int sparseoit_set_active(sparseoit_ctx *ctx, const uint8_t *d_mask, int64_t n, void *stream);
+
+/* The active index list (device, ascending, int32) and |A|.  The pointer
+ * stays valid until the next set_active. */
+int sparseoit_get_active(sparseoit_ctx *ctx, const int32_t **d_idx, int64_t *n_active);
+
+/* Sec. 4.1 / Alg. 2 (BAU): bring the frozen sums of `view` up to date with
+ * the current active set, for camera *cam (host struct).  INCREMENTAL is
+ * exact when the view was last committed under the previous active set and
+ * the splats of the complement (and sigma, c0, the camera) did not change
+ * since; otherwise the call falls back to RECOMPUTE.  A view that is
+ * already current is left as it is. */
+int sparseoit_commit_frozen(sparseoit_ctx *ctx, const sparseoit_splats *splats, const sparseoit_camera *cam,
+                            int32_t view, int32_t mode, void *stream);
+
+/* Device pointer to the frozen sums of `view`: 5 planes of H*W floats
+ * (P_r, P_g, P_b, Q, log T).  Valid until destroy. */
+int sparseoit_get_frozen(sparseoit_ctx *ctx, int32_t view, float **d_planes);
+
+/* Alg. 1 / Alg. 2 (BAN): render the active set of n_views views in one
+ * batched launch sequence and compose each with its frozen sums (Eq. 7).
+ *   cams[k] (host) is the camera of view views[k] (host int array);
+ *   d_images[k] (device [H, W, 3]) receives the image of view views[k].
+ *   d_targets: NULL, or n_views device images [H, W, 3].  With targets the
+ *     L1 loss  L = sum_k mean_{pixels, channels} |C_k - I_k|  is written to
+ *     d_loss (device float, overwritten) and the backward needs no
+ *     d_grad_images (dL/dC = sign(C - I) / (3 H W), sign(0) = 0).
+ * Every listed view must be committed under the current active set, else
+ * SPARSEOIT_ERR_STATE.  1 <= n_views <= SPARSEOIT_MAX_BATCH_VIEWS, no view
+ * listed twice. */
+int sparseoit_forward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const sparseoit_camera *cams,
+                      const int32_t *views, int32_t n_views, float *const *d_images, const float *const *d_targets,
+                      float *d_loss, void *stream);
+
+/* App. B / Sec. 4.2: gradients of the last forward's loss with respect to the
+ * active splats' parameters (summed over its views).  d_grad_images: NULL
+ * when that forward had targets (fused L1), else n_views device arrays
+ * [H, W, 3] holding dL/dC in the forward's view order.  `splats` must be the
+ * same parameter values as in the forward. */
+int sparseoit_backward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const float *const *d_grad_images,
+                       sparseoit_grads *out, void *stream);
+
+/* Enlarge the pair arena to at least max_pairs entries (synchronises). */
+int sparseoit_reserve_pairs(sparseoit_ctx *ctx, int64_t max_pairs);
+
+/* Synchronise `stream`, read and clear the device status word.  Returns
+ * SPARSEOIT_ERR_CAPACITY if a pair arena overflowed since the last call,
+ * SPARSEOIT_ERR_TIMEOUT if a bounded wait gave up, else SPARSEOIT_OK. */
+int sparseoit_status(sparseoit_ctx *ctx, void *stream);
+
+/* Counters of the last forward (synchronises `stream`): number of
+ * (splat, tile) pairs binned (M, summed over its views) and the number of
+ * (splat, pixel) pairs with alpha >= 1/255 (E, counted by the forward
+ * raster when counting is enabled with sparseoit_set_counting). */
+int sparseoit_last_counts(sparseoit_ctx *ctx, void *stream, int64_t *n_pairs, int64_t *n_contrib);
+
+/* Enable (1) / disable (0) the contributing-pair counter of the forward
+ * raster (off by default; costs one atomic per thread block). */
+int sparseoit_set_counting(sparseoit_ctx *ctx, int32_t enable);
+
+/* Last error message of the context (or of the last failed create when ctx
+ * is NULL).  Never NULL. */
+const char *sparseoit_last_error(const sparseoit_ctx *ctx);
+
+/* SPARSEOIT_ABI_VERSION of the loaded library. */
+int sparseoit_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPARSEOIT_H */

@@ -1,0 +1,497 @@
+// api.cu -- the C ABI of libsparseoit (declared in include/sparseoit.h).
+//
+// A context holds the active-set state (masks, compacted index lists and
+// the deltas of the last change), one set of frozen sums per training view
+// with the active-set generation it was committed under, and the workspace
+// of one batched forward / backward: projected records, tile counts /
+// offsets, the pair arena, the pixel states and the screen-space gradients.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sparseoit.h"
+#include "common.cuh"
+#include "launch.h"
+
+using namespace soit;
+
+struct sparseoit_ctx {
+    int64_t N = 0;
+    int n_views = 0;
+    std::vector<int> W, H;
+    int64_t pair_cap = 0;
+    std::string err;
+
+    // active set
+    uint8_t *d_mask[2] = {nullptr, nullptr};
+    int cur = 0;
+    int *d_idx_active = nullptr, *d_idx_comp = nullptr, *d_idx_plus = nullptr, *d_idx_minus = nullptr;
+    int *d_blk = nullptr;
+    int64_t *d_totals = nullptr;
+    int64_t *h_totals = nullptr;  // pinned
+    int64_t n_active = 0, n_comp = 0, n_plus = 0, n_minus = 0;
+    int64_t generation = 0;       // number of set_active calls
+    bool have_mask = false;
+    std::vector<int64_t> view_gen;
+    std::vector<float *> d_frozen;
+
+    // batch workspace
+    float4 *d_rec = nullptr, *d_ext = nullptr;
+    int64_t rec_cap = 0;          // records
+    int *d_tile_count = nullptr, *d_offsets = nullptr, *d_cursor = nullptr;
+    int64_t tile_cap = 0;
+    uint32_t *d_pairs = nullptr;
+    std::vector<float *> d_state;  // per batch slot, 6 planes of the largest view
+    int64_t max_pix = 0;
+    float4 *d_sgrad = nullptr;
+    int64_t sgrad_cap = 0;        // records
+    unsigned *d_status = nullptr;
+    int64_t *d_npairs = nullptr;
+    unsigned long long *d_contrib = nullptr;
+    bool counting = false;
+
+    // last forward
+    bool have_fwd = false;
+    bool last_fused = false;
+    Batch last_batch;
+    int last_n_list = 0;
+    int64_t last_generation = -1;
+};
+
+static std::string g_create_err;
+
+static int fail(sparseoit_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg; else g_create_err = msg;
+    return code;
+}
+
+static int cuda_check(sparseoit_ctx *c, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return SPARSEOIT_OK;
+    const int code = (e == cudaErrorMemoryAllocation) ? SPARSEOIT_ERR_OOM : SPARSEOIT_ERR_CUDA;
+    return fail(c, code, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                              \
+    do {                                                            \
+        int rc__ = cuda_check(ctx, (call), what);                   \
+        if (rc__ != SPARSEOIT_OK) return rc__;                      \
+    } while (0)
+
+#define CK_LAUNCH(what) CK(cudaGetLastError(), what)
+
+template <typename T>
+static cudaError_t grow(T **p, int64_t *cap, int64_t want) {
+    if (*p && *cap >= want) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    const int64_t n = want > 0 ? want : 1;
+    cudaError_t e = cudaMalloc((void **)p, (size_t)n * sizeof(T));
+    if (e == cudaSuccess) *cap = n;
+    return e;
+}
+
+static int check_splats(sparseoit_ctx *ctx, const sparseoit_splats *s) {
+    if (!s) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "splats is null");
+    if (s->n != ctx->N) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "splats->n differs from max_splats");
+    if (!s->means || !s->quats || !s->log_scales || !s->opacity_logits || !s->sh_color || !s->sh_weight)
+        return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "a splat parameter pointer is null");
+    if (((uintptr_t)s->quats & 15u) != 0)
+        return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "quats must be 16-byte aligned");
+    if (s->sh_dtype != SPARSEOIT_F32 && s->sh_dtype != SPARSEOIT_BF16)
+        return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "unknown sh_dtype");
+    if (!(s->sigma > 0.f)) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "sigma must be > 0");
+    return SPARSEOIT_OK;
+}
+
+static SplatPtrs splat_ptrs(const sparseoit_splats *s) {
+    SplatPtrs p;
+    p.means = s->means;
+    p.quats = s->quats;
+    p.log_scales = s->log_scales;
+    p.opacity_logits = s->opacity_logits;
+    p.sh_color = s->sh_color;
+    p.sh_weight = s->sh_weight;
+    p.sigma = s->sigma;
+    for (int k = 0; k < 3; ++k) p.bg[k] = s->bg[k];
+    return p;
+}
+
+static int fill_view(sparseoit_ctx *ctx, const sparseoit_camera *cam, int view, ViewDesc &vd, int tile_base) {
+    if (!cam) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "camera is null");
+    if (view < 0 || view >= ctx->n_views) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "view index out of range");
+    if (cam->width != ctx->W[view] || cam->height != ctx->H[view])
+        return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "camera size differs from the view's size");
+    if (!(cam->fx > 0.f) || !(cam->fy > 0.f)) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "focal length must be > 0");
+    memset(&vd, 0, sizeof(vd));
+    memcpy(vd.R, cam->R, sizeof(vd.R));
+    memcpy(vd.t, cam->t, sizeof(vd.t));
+    vd.fx = cam->fx; vd.fy = cam->fy; vd.cx = cam->cx; vd.cy = cam->cy;
+    for (int i = 0; i < 3; ++i)
+        vd.campos[i] = -(cam->R[0 * 3 + i] * cam->t[0] + cam->R[1 * 3 + i] * cam->t[1] + cam->R[2 * 3 + i] * cam->t[2]);
+    vd.W = cam->width;
+    vd.H = cam->height;
+    vd.tiles_x = (vd.W + kTile - 1) / kTile;
+    vd.tiles_y = (vd.H + kTile - 1) / kTile;
+    vd.tile_base = tile_base;
+    vd.frozen = ctx->d_frozen[view];
+    return SPARSEOIT_OK;
+}
+
+// Project list (list1: sign +1, list2: sign -1) into the batch's records and
+// bin them by tile.  b.n_list / tile bases must be set.
+static int render_pass_bin(sparseoit_ctx *ctx, Batch &b, const sparseoit_splats *s, const int *list1, int n1,
+                           const int *list2, int n2, cudaStream_t st) {
+    const int64_t nrec = (int64_t)b.n_views * (n1 + n2);
+    if (nrec > 0xffffffffll) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "too many records in one batch");
+    if (ctx->rec_cap < 3 * nrec || ctx->tile_cap < (int64_t)b.total_tiles + 1)
+        return fail(ctx, SPARSEOIT_ERR_STATE, "batch workspace not sized");
+    CK(cudaMemsetAsync(ctx->d_tile_count, 0, (size_t)b.total_tiles * sizeof(int), st), "memset(tile counts)");
+    const SplatPtrs sp = splat_ptrs(s);
+    launch_project(b, sp, s->sh_dtype == SPARSEOIT_BF16, list1, n1, list2, n2, ctx->d_rec, ctx->d_ext,
+                   ctx->d_tile_count, st);
+    CK_LAUNCH("project_kernel");
+    launch_scan_tiles(ctx->d_tile_count, b.total_tiles, ctx->d_offsets, ctx->d_cursor, ctx->pair_cap, ctx->d_status,
+                      ctx->d_npairs, st);
+    CK_LAUNCH("scan_tiles_kernel");
+    launch_scatter(b, ctx->d_rec, ctx->d_ext, ctx->d_cursor, ctx->d_pairs, ctx->pair_cap, st);
+    CK_LAUNCH("scatter_kernel");
+    return SPARSEOIT_OK;
+}
+
+// Records, ext, tile arrays sized for a batch.
+static int ensure_batch_ws(sparseoit_ctx *ctx, int64_t nrec, int64_t tiles) {
+    if (ctx->rec_cap < 3 * nrec) {
+        if (ctx->d_rec) cudaFree(ctx->d_rec);
+        if (ctx->d_ext) cudaFree(ctx->d_ext);
+        ctx->d_rec = nullptr;
+        ctx->d_ext = nullptr;
+        ctx->rec_cap = 0;
+        const int64_t n = nrec > 0 ? nrec : 1;
+        CK(cudaMalloc((void **)&ctx->d_rec, (size_t)(3 * n) * sizeof(float4)), "cudaMalloc(records)");
+        CK(cudaMalloc((void **)&ctx->d_ext, (size_t)n * sizeof(float4)), "cudaMalloc(ext)");
+        ctx->rec_cap = 3 * n;
+    }
+    if (ctx->tile_cap < tiles + 1) {
+        if (ctx->d_tile_count) cudaFree(ctx->d_tile_count);
+        if (ctx->d_offsets) cudaFree(ctx->d_offsets);
+        if (ctx->d_cursor) cudaFree(ctx->d_cursor);
+        ctx->d_tile_count = ctx->d_offsets = ctx->d_cursor = nullptr;
+        ctx->tile_cap = 0;
+        const int64_t n = tiles + 1;
+        CK(cudaMalloc((void **)&ctx->d_tile_count, (size_t)n * sizeof(int)), "cudaMalloc(tile counts)");
+        CK(cudaMalloc((void **)&ctx->d_offsets, (size_t)n * sizeof(int)), "cudaMalloc(tile offsets)");
+        CK(cudaMalloc((void **)&ctx->d_cursor, (size_t)n * sizeof(int)), "cudaMalloc(tile cursors)");
+        ctx->tile_cap = n;
+    }
+    return SPARSEOIT_OK;
+}
+
+extern "C" {
+
+int sparseoit_version(void) { return SPARSEOIT_ABI_VERSION; }
+
+const char *sparseoit_last_error(const sparseoit_ctx *ctx) {
+    if (!ctx) return g_create_err.c_str();
+    return ctx->err.c_str();
+}
+
+int sparseoit_create(sparseoit_ctx **out, int64_t max_splats, int32_t n_views, const int32_t *view_w,
+                     const int32_t *view_h, const sparseoit_config *cfg) {
+    if (!out) return fail(nullptr, SPARSEOIT_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    if (max_splats < 0 || max_splats > 0x7fffffffll)
+        return fail(nullptr, SPARSEOIT_ERR_INVALID_ARG, "max_splats out of range");
+    if (n_views < 1 || !view_w || !view_h) return fail(nullptr, SPARSEOIT_ERR_INVALID_ARG, "need >= 1 view");
+    for (int v = 0; v < n_views; ++v)
+        if (view_w[v] < 1 || view_h[v] < 1 || view_w[v] > 16384 || view_h[v] > 16384)
+            return fail(nullptr, SPARSEOIT_ERR_INVALID_ARG, "view size out of range");
+    sparseoit_ctx *ctx = new sparseoit_ctx();
+    ctx->N = max_splats;
+    ctx->n_views = n_views;
+    ctx->pair_cap = (cfg && cfg->max_pairs > 0) ? cfg->max_pairs : (int64_t)1 << 25;
+    if (ctx->pair_cap > 0x7fffffffll) ctx->pair_cap = 0x7fffffffll;
+    ctx->view_gen.assign(n_views, -1);
+    ctx->d_frozen.assign(n_views, nullptr);
+    auto bail = [&](int rc) {
+        g_create_err = ctx->err;
+        sparseoit_destroy(ctx);
+        return rc;
+    };
+    for (int v = 0; v < n_views; ++v) {
+        ctx->W.push_back(view_w[v]);
+        ctx->H.push_back(view_h[v]);
+        const int64_t hw = (int64_t)view_w[v] * view_h[v];
+        if (hw > ctx->max_pix) ctx->max_pix = hw;
+        cudaError_t e = cudaMalloc((void **)&ctx->d_frozen[v], (size_t)(5 * hw) * sizeof(float));
+        if (e != cudaSuccess) return bail(cuda_check(ctx, e, "cudaMalloc(frozen sums)"));
+        e = cudaMemset(ctx->d_frozen[v], 0, (size_t)(5 * hw) * sizeof(float));
+        if (e != cudaSuccess) return bail(cuda_check(ctx, e, "cudaMemset(frozen sums)"));
+    }
+    const int64_t n = max_splats > 0 ? max_splats : 1;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_mask[0], (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_mask[1], (size_t)n);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_mask[0], 0, (size_t)n);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_mask[1], 0, (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_idx_active, (size_t)n * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_idx_comp, (size_t)n * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_idx_plus, (size_t)n * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_idx_minus, (size_t)n * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_blk, (size_t)compact_scratch_ints(n) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_totals, 4 * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->h_totals, 4 * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_pairs, (size_t)ctx->pair_cap * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_npairs, sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_npairs, 0, sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_contrib, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_contrib, 0, sizeof(unsigned long long));
+    if (e != cudaSuccess) return bail(cuda_check(ctx, e, "cudaMalloc(context)"));
+    *out = ctx;
+    return SPARSEOIT_OK;
+}
+
+int sparseoit_destroy(sparseoit_ctx *ctx) {
+    if (!ctx) return SPARSEOIT_OK;
+    cudaDeviceSynchronize();
+    for (float *p : ctx->d_frozen) if (p) cudaFree(p);
+    for (float *p : ctx->d_state) if (p) cudaFree(p);
+    void *bufs[] = {ctx->d_mask[0], ctx->d_mask[1], ctx->d_idx_active, ctx->d_idx_comp, ctx->d_idx_plus,
+                    ctx->d_idx_minus, ctx->d_blk, ctx->d_totals, ctx->d_rec, ctx->d_ext, ctx->d_tile_count,
+                    ctx->d_offsets, ctx->d_cursor, ctx->d_pairs, ctx->d_sgrad, ctx->d_status, ctx->d_npairs,
+                    ctx->d_contrib};
+    for (void *p : bufs) if (p) cudaFree(p);
+    if (ctx->h_totals) cudaFreeHost(ctx->h_totals);
+    delete ctx;
+    return SPARSEOIT_OK;
+}
+
+int sparseoit_set_active(sparseoit_ctx *ctx, const uint8_t *d_mask, int64_t n, void *stream) {
+    if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
+    if (!d_mask && n > 0) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "mask is null");
+    if (n != ctx->N) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "mask length differs from max_splats");
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint8_t *prev = ctx->have_mask ? ctx->d_mask[ctx->cur] : nullptr;
+    uint8_t *store = ctx->d_mask[ctx->cur ^ 1];
+    launch_compact(d_mask, prev, n, ctx->d_blk, ctx->d_totals, ctx->d_idx_active, ctx->d_idx_comp, ctx->d_idx_plus,
+                   ctx->d_idx_minus, store, st);
+    CK_LAUNCH("compaction kernels");
+    CK(cudaMemcpyAsync(ctx->h_totals, ctx->d_totals, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, st),
+       "copy active counts");
+    CK(cudaStreamSynchronize(st), "set_active sync");
+    ctx->n_active = ctx->h_totals[0];
+    ctx->n_comp = ctx->h_totals[1];
+    ctx->n_plus = ctx->h_totals[2];
+    ctx->n_minus = ctx->h_totals[3];
+    ctx->cur ^= 1;
+    ctx->have_mask = true;
+    ctx->generation += 1;
+    ctx->have_fwd = false;
+    return SPARSEOIT_OK;
+}
+
+int sparseoit_get_active(sparseoit_ctx *ctx, const int32_t **d_idx, int64_t *n_active) {
+    if (!ctx || !d_idx || !n_active) return SPARSEOIT_ERR_INVALID_ARG;
+    if (!ctx->have_mask) return fail(ctx, SPARSEOIT_ERR_STATE, "no active set yet");
+    *d_idx = ctx->d_idx_active;
+    *n_active = ctx->n_active;
+    return SPARSEOIT_OK;
+}
+
+int sparseoit_get_frozen(sparseoit_ctx *ctx, int32_t view, float **d_planes) {
+    if (!ctx || !d_planes) return SPARSEOIT_ERR_INVALID_ARG;
+    if (view < 0 || view >= ctx->n_views) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "view index out of range");
+    *d_planes = ctx->d_frozen[view];
+    return SPARSEOIT_OK;
+}
+
+int sparseoit_commit_frozen(sparseoit_ctx *ctx, const sparseoit_splats *splats, const sparseoit_camera *cam,
+                            int32_t view, int32_t mode, void *stream) {
+    if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
+    int rc = check_splats(ctx, splats);
+    if (rc) return rc;
+    if (!ctx->have_mask) return fail(ctx, SPARSEOIT_ERR_STATE, "commit before set_active");
+    if (mode != SPARSEOIT_COMMIT_INCREMENTAL && mode != SPARSEOIT_COMMIT_RECOMPUTE)
+        return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "unknown commit mode");
+    if (view < 0 || view >= ctx->n_views) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "view index out of range");
+    if (ctx->view_gen[view] == ctx->generation) return SPARSEOIT_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    Batch b;
+    memset(&b, 0, sizeof(b));
+    b.n_views = 1;
+    rc = fill_view(ctx, cam, view, b.v[0], 0);
+    if (rc) return rc;
+    b.total_tiles = b.v[0].tiles_x * b.v[0].tiles_y;
+    const bool incremental = mode == SPARSEOIT_COMMIT_INCREMENTAL && ctx->view_gen[view] == ctx->generation - 1;
+    const int *l1, *l2 = nullptr;
+    int64_t n1, n2 = 0;
+    if (incremental) {
+        l1 = ctx->d_idx_plus; n1 = ctx->n_plus;
+        l2 = ctx->d_idx_minus; n2 = ctx->n_minus;
+    } else {
+        const int64_t hw = (int64_t)ctx->W[view] * ctx->H[view];
+        CK(cudaMemsetAsync(ctx->d_frozen[view], 0, (size_t)(5 * hw) * sizeof(float), st), "memset(frozen)");
+        l1 = ctx->d_idx_comp; n1 = ctx->n_comp;
+    }
+    b.n_list = (int)(n1 + n2);
+    ctx->have_fwd = false;  // the commit reuses the forward's workspace
+    if (b.n_list > 0) {
+        rc = ensure_batch_ws(ctx, b.n_list, b.total_tiles);
+        if (rc) return rc;
+        rc = render_pass_bin(ctx, b, splats, l1, (int)n1, l2, (int)n2, st);
+        if (rc) return rc;
+        launch_raster_fwd(b, kRasterSums, ctx->d_rec, ctx->d_offsets, ctx->d_pairs, ctx->pair_cap, splats->bg, nullptr,
+                          nullptr, st);
+        CK_LAUNCH("raster_fwd_kernel(sums)");
+    }
+    ctx->view_gen[view] = ctx->generation;
+    return SPARSEOIT_OK;
+}
+
+int sparseoit_forward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const sparseoit_camera *cams,
+                      const int32_t *views, int32_t n_views, float *const *d_images, const float *const *d_targets,
+                      float *d_loss, void *stream) {
+    if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
+    int rc = check_splats(ctx, splats);
+    if (rc) return rc;
+    if (!ctx->have_mask) return fail(ctx, SPARSEOIT_ERR_STATE, "forward before set_active");
+    if (n_views < 1 || n_views > kMaxViews || !cams || !views || !d_images)
+        return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "bad view list");
+    if (d_targets && !d_loss) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "targets given without a loss pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    Batch b;
+    memset(&b, 0, sizeof(b));
+    b.n_views = n_views;
+    int tiles = 0;
+    for (int k = 0; k < n_views; ++k) {
+        const int v = views[k];
+        if (v < 0 || v >= ctx->n_views) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "view index out of range");
+        for (int j = 0; j < k; ++j)
+            if (views[j] == v) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "a view is listed twice");
+        if (ctx->view_gen[v] != ctx->generation)
+            return fail(ctx, SPARSEOIT_ERR_STATE, "frozen sums of view " + std::to_string(v) +
+                                                      " are stale: call sparseoit_commit_frozen first");
+        rc = fill_view(ctx, &cams[k], v, b.v[k], tiles);
+        if (rc) return rc;
+        if (!d_images[k]) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "image pointer is null");
+        b.v[k].image = d_images[k];
+        if (d_targets) {
+            if (!d_targets[k]) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "target pointer is null");
+            b.v[k].target = d_targets[k];
+        }
+        tiles += b.v[k].tiles_x * b.v[k].tiles_y;
+    }
+    b.total_tiles = tiles;
+    b.n_list = (int)ctx->n_active;
+    while ((int)ctx->d_state.size() < n_views) ctx->d_state.push_back(nullptr);
+    for (int k = 0; k < n_views; ++k) {
+        if (!ctx->d_state[k]) CK(cudaMalloc((void **)&ctx->d_state[k], (size_t)(6 * ctx->max_pix) * sizeof(float)),
+                                 "cudaMalloc(pixel state)");
+        b.v[k].state = ctx->d_state[k];
+    }
+    rc = ensure_batch_ws(ctx, (int64_t)n_views * ctx->n_active, tiles);
+    if (rc) return rc;
+    if (d_loss) CK(cudaMemsetAsync(d_loss, 0, sizeof(float), st), "memset(loss)");
+    if (ctx->counting) CK(cudaMemsetAsync(ctx->d_contrib, 0, sizeof(unsigned long long), st), "memset(counter)");
+    rc = render_pass_bin(ctx, b, splats, ctx->d_idx_active, (int)ctx->n_active, nullptr, 0, st);
+    if (rc) return rc;
+    launch_raster_fwd(b, d_targets ? kRasterFused : kRasterAux, ctx->d_rec, ctx->d_offsets, ctx->d_pairs,
+                      ctx->pair_cap, splats->bg, d_targets ? d_loss : nullptr, ctx->counting ? ctx->d_contrib : nullptr,
+                      st);
+    CK_LAUNCH("raster_fwd_kernel");
+    ctx->have_fwd = true;
+    ctx->last_fused = d_targets != nullptr;
+    ctx->last_batch = b;
+    ctx->last_n_list = (int)ctx->n_active;
+    ctx->last_generation = ctx->generation;
+    return SPARSEOIT_OK;
+}
+
+int sparseoit_backward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const float *const *d_grad_images,
+                       sparseoit_grads *out, void *stream) {
+    if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
+    int rc = check_splats(ctx, splats);
+    if (rc) return rc;
+    if (!ctx->have_fwd || ctx->last_generation != ctx->generation)
+        return fail(ctx, SPARSEOIT_ERR_STATE, "backward without a matching forward");
+    if (!out || !out->means || !out->quats || !out->log_scales || !out->opacity_logits || !out->sh_color ||
+        !out->sh_weight || !out->sigma)
+        return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "a gradient pointer is null");
+    if (((uintptr_t)out->quats & 15u) || ((uintptr_t)out->sh_color & 15u) || ((uintptr_t)out->sh_weight & 15u))
+        return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "quats / sh gradients must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    Batch &b = ctx->last_batch;
+    if (!ctx->last_fused) {
+        if (!d_grad_images) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "grad images needed (forward had no targets)");
+        for (int k = 0; k < b.n_views; ++k) {
+            if (!d_grad_images[k]) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "grad image pointer is null");
+            b.v[k].grad_image = d_grad_images[k];
+        }
+        launch_prep_state(b, splats->bg, st);
+        CK_LAUNCH("prep_state_kernel");
+    }
+    const int64_t nrec = (int64_t)b.n_views * ctx->last_n_list;
+    CK(grow(&ctx->d_sgrad, &ctx->sgrad_cap, 3 * nrec), "cudaMalloc(screen grads)");
+    CK(cudaMemsetAsync(ctx->d_sgrad, 0, (size_t)(3 * nrec) * sizeof(float4), st), "memset(screen grads)");
+    launch_raster_bwd(b, ctx->d_rec, ctx->d_offsets, ctx->d_pairs, ctx->pair_cap, ctx->d_sgrad, st);
+    CK_LAUNCH("raster_bwd_kernel");
+    CK(cudaMemsetAsync(out->sigma, 0, sizeof(float), st), "memset(dsigma)");
+    GradPtrs g{out->means,    out->quats,     out->log_scales, out->opacity_logits,
+               out->sh_color, out->sh_weight, out->sigma,      out->rows_by_splat != 0};
+    launch_project_bwd(b, splat_ptrs(splats), splats->sh_dtype == SPARSEOIT_BF16, ctx->d_idx_active, ctx->last_n_list,
+                       ctx->d_sgrad, g, st);
+    CK_LAUNCH("project_bwd_kernel");
+    return SPARSEOIT_OK;
+}
+
+int sparseoit_reserve_pairs(sparseoit_ctx *ctx, int64_t max_pairs) {
+    if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
+    if (max_pairs <= ctx->pair_cap) return SPARSEOIT_OK;
+    if (max_pairs > 0x7fffffffll) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "max_pairs above 2^31 - 1");
+    CK(cudaDeviceSynchronize(), "reserve sync");
+    if (ctx->d_pairs) cudaFree(ctx->d_pairs);
+    ctx->d_pairs = nullptr;
+    ctx->pair_cap = 0;
+    CK(cudaMalloc((void **)&ctx->d_pairs, (size_t)max_pairs * sizeof(uint32_t)), "cudaMalloc(pairs)");
+    ctx->pair_cap = max_pairs;
+    ctx->have_fwd = false;
+    return SPARSEOIT_OK;
+}
+
+int sparseoit_status(sparseoit_ctx *ctx, void *stream) {
+    if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned h = 0;
+    CK(cudaMemcpyAsync(&h, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "read status");
+    CK(cudaStreamSynchronize(st), "status sync");
+    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), st), "clear status");
+    CK(cudaStreamSynchronize(st), "status sync");
+    if (h & kStatusCapacity) return fail(ctx, SPARSEOIT_ERR_CAPACITY, "pair arena overflow");
+    if (h & kStatusTimeout) return fail(ctx, SPARSEOIT_ERR_TIMEOUT, "a device-side wait gave up");
+    return SPARSEOIT_OK;
+}
+
+int sparseoit_last_counts(sparseoit_ctx *ctx, void *stream, int64_t *n_pairs, int64_t *n_contrib) {
+    if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t hp = 0;
+    unsigned long long hc = 0;
+    CK(cudaMemcpyAsync(&hp, ctx->d_npairs, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "read pair count");
+    CK(cudaMemcpyAsync(&hc, ctx->d_contrib, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st),
+       "read contrib count");
+    CK(cudaStreamSynchronize(st), "counts sync");
+    if (n_pairs) *n_pairs = hp;
+    if (n_contrib) *n_contrib = (int64_t)hc;
+    return SPARSEOIT_OK;
+}
+
+int sparseoit_set_counting(sparseoit_ctx *ctx, int32_t enable) {
+    if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
+    ctx->counting = enable != 0;
+    return SPARSEOIT_OK;
+}
+
+}  // extern "C"

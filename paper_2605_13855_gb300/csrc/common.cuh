@@ -1,0 +1,217 @@
+// common.cuh -- device-side definitions shared by the kernels of libsparseoit.
+//
+// Data layout in HBM (one batch = the views of one forward / commit call):
+//   * projected record of list entry r in batch view v: index q = v * n_list + r,
+//       rec[3q+0] = (mu'x, mu'y, r, A2)        quadratic form, see below
+//       rec[3q+1] = (B2, log2 o, w, c_r)
+//       rec[3q+2] = (c_g, c_b, sign, 0)        sign = +1 / -1 (frozen-sum update)
+//     ext[q] = (tau2', y half-extent, x half-extent, dy of the x extreme)
+//   * tile bins: one tile id space for all views of the batch (view v owns
+//     [tile_base, tile_base + tiles_x * tiles_y)); offsets[t] .. offsets[t+1]
+//     index the u32 pair arena that holds record indices q (no depth key).
+//   * per-pixel planes (H*W floats each): frozen sums (P_r, P_g, P_b, Q, log T)
+//     and the backward pixel state (g_r, g_g, g_b, A, B, g.F).
+//
+// The per-pair exponent is evaluated in a factored form of Eq. 5 that has no
+// cancellation for thin ellipses:  with Sigma' = [[sxx, sxy], [sxy, syy]],
+//     1/2 d^T Sigma'^-1 d = syy/(2 det) (dx - (sxy/syy) dy)^2 + dy^2/(2 syy),
+// so with L = log2(e), r = sxy/syy, A2 = sqrt(L syy / (2 det)),
+// B2 = sqrt(L / (2 syy)):
+//     log2 alpha_raw = log2 o - (A2 (dx - r dy))^2 - (B2 dy)^2.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace soit {
+
+constexpr int kTile = 16;                       // tile edge in pixels (App. A: 16x16 tiles)
+constexpr int kTilePix = kTile * kTile;         // 256 pixels = 8 warps (Sec. 4.2)
+constexpr int kMaxViews = 32;
+constexpr float kNearZ = 0.2f;                  // near-plane cull (3DGS convention)
+constexpr float kDilation = 0.3f;               // low-pass dilation of Sigma' (3DGS convention)
+constexpr float kAlphaMax = 0.99f;              // opacity clamp (3DGS convention)
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+constexpr float kLog2_255 = 7.9943534368588578f;  // log2(255); alpha_raw >= 1/255 <=> log2 alpha_raw >= -this
+
+constexpr unsigned kStatusCapacity = 1u;
+constexpr unsigned kStatusTimeout = 2u;
+
+struct ViewDesc {
+    float R[9], t[3];             // world -> camera
+    float fx, fy, cx, cy;
+    float campos[3];              // camera centre -R^T t
+    int W, H, tiles_x, tiles_y;
+    int tile_base;                // first batch tile id of this view
+    int pad_;
+    float *image;                 // [H, W, 3] output image (forward)
+    const float *target;          // [H, W, 3] L1 target (fused loss) or null
+    float *frozen;                // 5 planes: frozen sums of this view
+    float *state;                 // 6 planes: pixel state (or F, T, Q before prep)
+    const float *grad_image;      // [H, W, 3] dL/dC (unfused backward) or null
+};
+
+struct Batch {
+    int n_views;
+    int total_tiles;
+    int n_list;                   // list entries (records) per view
+    int pad_;
+    ViewDesc v[kMaxViews];
+};
+
+struct SplatPtrs {
+    const float *means, *quats, *log_scales, *opacity_logits;
+    const void *sh_color, *sh_weight;
+    float sigma;
+    float bg[3];
+};
+
+__device__ __forceinline__ int find_view(const Batch &b, int gt) {
+    int v = 0;
+    while (v + 1 < b.n_views && gt >= b.v[v + 1].tile_base) ++v;
+    return v;
+}
+
+// Clamp a float to [lo, hi] before converting (NaN -> lo).
+__device__ __forceinline__ int f2i_clamped(float f, int lo, int hi) {
+    if (!(f >= (float)lo)) return lo;
+    if (f >= (float)hi) return hi;
+    return (int)f;
+}
+
+template <typename T>
+__device__ __forceinline__ float ldf(const T *p, int64_t i);
+template <>
+__device__ __forceinline__ float ldf<float>(const float *p, int64_t i) { return __ldg(p + i); }
+template <>
+__device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16 *p, int64_t i) {
+    return __bfloat162float(p[i]);
+}
+
+// Real orthonormal spherical harmonics of degree <= 3 at the unit vector
+// (x, y, z), without the Condon-Shortley phase, index k = l^2 + l + m
+// (Eq. 4).  Each constant is sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times the
+// factors of the Cartesian polynomial (and sqrt 2 for m != 0), written out.
+namespace shc {
+constexpr float C0 = 0.28209479177387814f;   // sqrt(1/(4 pi))
+constexpr float C1 = 0.48860251190291992f;   // sqrt(3/(4 pi))
+constexpr float C2a = 1.0925484305920792f;   // sqrt(15/(4 pi))       xy, yz, xz
+constexpr float C2b = 0.31539156525252005f;  // sqrt(5/(16 pi))       3z^2 - 1
+constexpr float C2c = 0.54627421529603959f;  // sqrt(15/(16 pi))      x^2 - y^2
+constexpr float C3a = 0.59004358992664352f;  // sqrt(35/(32 pi))      3x^2 y - y^3, x^3 - 3 x y^2
+constexpr float C3b = 2.8906114426405538f;   // sqrt(105/(4 pi))      xyz
+constexpr float C3c = 0.45704579946446577f;  // sqrt(21/(32 pi))      y(5z^2-1), x(5z^2-1)
+constexpr float C3d = 0.37317633259011540f;  // sqrt(7/(16 pi))       z(5z^2 - 3)
+constexpr float C3e = 1.4453057213202771f;   // sqrt(105/(16 pi))     z(x^2 - y^2)
+}  // namespace shc
+
+__device__ __forceinline__ void sh_basis16(float x, float y, float z, float Y[16]) {
+    using namespace shc;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[0] = C0;
+    Y[1] = C1 * y;
+    Y[2] = C1 * z;
+    Y[3] = C1 * x;
+    Y[4] = C2a * x * y;
+    Y[5] = C2a * y * z;
+    Y[6] = C2b * (3.f * zz - 1.f);
+    Y[7] = C2a * x * z;
+    Y[8] = C2c * (xx - yy);
+    Y[9] = C3a * y * (3.f * xx - yy);
+    Y[10] = C3b * x * y * z;
+    Y[11] = C3c * y * (5.f * zz - 1.f);
+    Y[12] = C3d * z * (5.f * zz - 3.f);
+    Y[13] = C3c * x * (5.f * zz - 1.f);
+    Y[14] = C3e * z * (xx - yy);
+    Y[15] = C3a * x * (xx - 3.f * yy);
+}
+
+// Gradient, in (x, y, z) as free variables, of f = sum_k a_k Y_k.
+__device__ __forceinline__ void sh_grad16(float x, float y, float z, const float a[16], float g[3]) {
+    using namespace shc;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    gy += a[1] * C1;
+    gz += a[2] * C1;
+    gx += a[3] * C1;
+    gx += a[4] * C2a * y;              gy += a[4] * C2a * x;
+    gy += a[5] * C2a * z;              gz += a[5] * C2a * y;
+    gz += a[6] * 6.f * C2b * z;
+    gx += a[7] * C2a * z;              gz += a[7] * C2a * x;
+    gx += a[8] * 2.f * C2c * x;        gy -= a[8] * 2.f * C2c * y;
+    gx += a[9] * 6.f * C3a * x * y;    gy += a[9] * 3.f * C3a * (xx - yy);
+    gx += a[10] * C3b * y * z;         gy += a[10] * C3b * x * z;   gz += a[10] * C3b * x * y;
+    gy += a[11] * C3c * (5.f * zz - 1.f);  gz += a[11] * 10.f * C3c * y * z;
+    gz += a[12] * C3d * (15.f * zz - 3.f);
+    gx += a[13] * C3c * (5.f * zz - 1.f);  gz += a[13] * 10.f * C3c * x * z;
+    gx += a[14] * 2.f * C3e * x * z;   gy -= a[14] * 2.f * C3e * y * z;  gz += a[14] * C3e * (xx - yy);
+    gx += a[15] * 3.f * C3a * (xx - yy);   gy -= a[15] * 6.f * C3a * x * y;
+    g[0] = gx; g[1] = gy; g[2] = gz;
+}
+
+// Rotation of the unit quaternion (w, x, y, z), row-major.
+__device__ __forceinline__ void quat_rot(float a, float b, float c, float d, float R[9]) {
+    R[0] = 1.f - 2.f * (c * c + d * d); R[1] = 2.f * (b * c - a * d);       R[2] = 2.f * (b * d + a * c);
+    R[3] = 2.f * (b * c + a * d);       R[4] = 1.f - 2.f * (b * b + d * d); R[5] = 2.f * (c * d - a * b);
+    R[6] = 2.f * (b * d - a * c);       R[7] = 2.f * (c * d + a * b);       R[8] = 1.f - 2.f * (b * b + c * c);
+}
+
+// Geometry of one splat in one view (Eq. 2 and Eq. 6), shared by the forward
+// projection and the backward chain so that both see identical values.
+struct SplatGeom {
+    float tc[3];          // camera-space centre
+    float s[3];           // axis scales
+    float Rq[9];          // rotation of the unit quaternion
+    float qn[4], qlen;    // unit quaternion, |q|
+    float Qm[9];          // W Rq
+    float n0[3], n1[3];   // rows of N = J W Rq S
+    float sxx, sxy, syy, det;
+    float d[3], dlen;     // mu - camera centre, its length
+};
+
+__device__ __forceinline__ bool splat_geometry(const ViewDesc &vd, const float mu[3], const float q[4],
+                                               const float ls[3], SplatGeom &g) {
+    for (int r = 0; r < 3; ++r)
+        g.tc[r] = fmaf(vd.R[3 * r + 0], mu[0], fmaf(vd.R[3 * r + 1], mu[1], fmaf(vd.R[3 * r + 2], mu[2], vd.t[r])));
+    const float z = g.tc[2];
+    if (!(z > kNearZ)) return false;
+    g.qlen = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    const float iq = 1.f / g.qlen;
+    for (int k = 0; k < 4; ++k) g.qn[k] = q[k] * iq;
+    quat_rot(g.qn[0], g.qn[1], g.qn[2], g.qn[3], g.Rq);
+    for (int k = 0; k < 3; ++k) g.s[k] = expf(ls[k]);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            g.Qm[3 * a + b] = fmaf(vd.R[3 * a + 0], g.Rq[0 * 3 + b],
+                                   fmaf(vd.R[3 * a + 1], g.Rq[1 * 3 + b], vd.R[3 * a + 2] * g.Rq[2 * 3 + b]));
+    // rows of J: j0 = (fx/z, 0, -fx x/z^2), j1 = (0, fy/z, -fy y/z^2)
+    const float iz = 1.f / z;
+    const float j00 = vd.fx * iz, j02 = -vd.fx * g.tc[0] * iz * iz;
+    const float j11 = vd.fy * iz, j12 = -vd.fy * g.tc[1] * iz * iz;
+    for (int b = 0; b < 3; ++b) {
+        g.n0[b] = fmaf(j00, g.Qm[0 * 3 + b], j02 * g.Qm[2 * 3 + b]) * g.s[b];
+        g.n1[b] = fmaf(j11, g.Qm[1 * 3 + b], j12 * g.Qm[2 * 3 + b]) * g.s[b];
+    }
+    const float nn0 = g.n0[0] * g.n0[0] + g.n0[1] * g.n0[1] + g.n0[2] * g.n0[2];
+    const float nn1 = g.n1[0] * g.n1[0] + g.n1[1] * g.n1[1] + g.n1[2] * g.n1[2];
+    g.sxx = nn0 + kDilation;
+    g.syy = nn1 + kDilation;
+    g.sxy = g.n0[0] * g.n1[0] + g.n0[1] * g.n1[1] + g.n0[2] * g.n1[2];
+    // det(N N^T) = |n0 x n1|^2 (Cauchy-Binet).  n0 x n1 = fx fy s0 s1 s2 / z^3
+    // * (Rq^T (mu - campos)) / s (componentwise), a sum of squares with no
+    // cancellation; det(N N^T + 0.3 I) = det(N N^T) + 0.3 tr(N N^T) + 0.09.
+    for (int k = 0; k < 3; ++k) g.d[k] = mu[k] - vd.campos[k];
+    g.dlen = sqrtf(g.d[0] * g.d[0] + g.d[1] * g.d[1] + g.d[2] * g.d[2]);
+    float cb = 0.f;
+    for (int k = 0; k < 3; ++k) {
+        float lk = (g.Rq[0 * 3 + k] * g.d[0] + g.Rq[1 * 3 + k] * g.d[1] + g.Rq[2 * 3 + k] * g.d[2]) / g.s[k];
+        cb = fmaf(lk, lk, cb);
+    }
+    const float kz = vd.fx * vd.fy * g.s[0] * g.s[1] * g.s[2] * iz * iz * iz;
+    const float detNN = kz * kz * cb;
+    g.det = detNN + kDilation * (nn0 + nn1) + kDilation * kDilation;
+    return true;
+}
+
+}  // namespace soit

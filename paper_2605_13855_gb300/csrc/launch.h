@@ -1,0 +1,34 @@
+// launch.h -- host-side launchers of the kernels (internal to libsparseoit).
+#pragma once
+#include "common.cuh"
+
+namespace soit {
+
+int launch_project(const Batch &b, const SplatPtrs &sp, bool bf16, const int *list1, int n1, const int *list2, int n2,
+                   float4 *rec, float4 *ext, int *tile_count, cudaStream_t st);
+int launch_scan_tiles(const int *count, int total, int *offsets, int *cursor, int64_t cap, unsigned *status,
+                      int64_t *pairs_out, cudaStream_t st);
+int launch_scatter(const Batch &b, const float4 *rec, const float4 *ext, int *cursor, uint32_t *pairs, int64_t cap,
+                   cudaStream_t st);
+
+enum RasterMode { kRasterFused = 0, kRasterAux = 1, kRasterSums = 2 };
+int launch_raster_fwd(const Batch &b, int mode, const float4 *rec, const int *offsets, const uint32_t *pairs,
+                      int64_t cap, const float bg[3], float *loss, unsigned long long *contrib, cudaStream_t st);
+
+int launch_prep_state(const Batch &b, const float bg[3], cudaStream_t st);
+int launch_raster_bwd(const Batch &b, const float4 *rec, const int *offsets, const uint32_t *pairs, int64_t cap,
+                      float4 *sgrad, cudaStream_t st);
+
+struct GradPtrs {
+    float *means, *quats, *log_scales, *opacity_logits, *sh_color, *sh_weight, *sigma;
+    int rows_by_splat;
+};
+int launch_project_bwd(const Batch &b, const SplatPtrs &sp, bool bf16, const int *list, int n, const float4 *sgrad,
+                       GradPtrs out, cudaStream_t st);
+
+int launch_compact(const uint8_t *mask_new, const uint8_t *mask_prev, int64_t n, int *blk_counts, int64_t *totals,
+                   int *idx_active, int *idx_comp, int *idx_plus, int *idx_minus, uint8_t *mask_store,
+                   cudaStream_t st);
+int64_t compact_scratch_ints(int64_t n);
+
+}  // namespace soit

@@ -1,0 +1,290 @@
+"""Python binding of libsparseoit: argument marshalling only.
+
+Every step of the renderer runs in the library's CUDA kernels; this module
+passes device pointers of PyTorch tensors and the current CUDA stream
+through the C ABI (include/sparseoit.h).  PyTorch supplies device memory,
+streams and autograd plumbing.  There is no CPU fallback: without the built
+library or a CUDA device every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import SparseOITError
+
+PARAM_NAMES = ("means", "quats", "log_scales", "opacity_logits", "sh_color", "sh_weight")
+PARAM_SHAPES = {"means": (3,), "quats": (4,), "log_scales": (3,), "opacity_logits": (), "sh_color": (16, 3),
+                "sh_weight": (16,)}
+
+
+@dataclass
+class SplatParams:
+    """Splat parameters on the GPU (Sec. 3.1 / 3.2; Eq. 1 sigma, Eq. 7 c0)."""
+    means: torch.Tensor           # [N, 3] float32
+    quats: torch.Tensor           # [N, 4] float32 (w, x, y, z)
+    log_scales: torch.Tensor      # [N, 3] float32
+    opacity_logits: torch.Tensor  # [N]    float32
+    sh_color: torch.Tensor        # [N, 16, 3] float32 or bfloat16
+    sh_weight: torch.Tensor       # [N, 16]    float32 or bfloat16
+    sigma: float = 6.0
+    bg: Sequence[float] = field(default_factory=lambda: (0.0, 0.0, 0.0))
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    @staticmethod
+    def from_numpy(scene: dict, device="cuda", sh_dtype=torch.float32) -> "SplatParams":
+        def t(a, dt=torch.float32):
+            return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).to(device=device, dtype=dt)
+        return SplatParams(t(scene["means"]), t(scene["quats"]), t(scene["log_scales"]),
+                           t(scene["opacity_logits"]), t(scene["sh_color"], sh_dtype), t(scene["sh_weight"], sh_dtype),
+                           float(scene["sigma"]), tuple(float(x) for x in scene["bg"]))
+
+
+def _check_param(name, t: torch.Tensor, n: int):
+    want = (n,) + PARAM_SHAPES[name]
+    if tuple(t.shape) != want:
+        raise ValueError(f"{name}: shape {tuple(t.shape)} != {want}")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def splats_struct(p: SplatParams) -> _lib.Splats:
+    n = p.n
+    for name in PARAM_NAMES:
+        _check_param(name, getattr(p, name), n)
+    for name in ("means", "quats", "log_scales", "opacity_logits"):
+        if getattr(p, name).dtype != torch.float32:
+            raise ValueError(f"{name} must be float32")
+    if p.sh_color.dtype != p.sh_weight.dtype or p.sh_color.dtype not in (torch.float32, torch.bfloat16):
+        raise ValueError("sh_color / sh_weight must both be float32 or both bfloat16")
+    s = _lib.Splats()
+    s.means = p.means.data_ptr()
+    s.quats = p.quats.data_ptr()
+    s.log_scales = p.log_scales.data_ptr()
+    s.opacity_logits = p.opacity_logits.data_ptr()
+    s.sh_color = p.sh_color.data_ptr()
+    s.sh_weight = p.sh_weight.data_ptr()
+    s.sh_dtype = _lib.BF16 if p.sh_color.dtype == torch.bfloat16 else _lib.F32
+    s.sigma = float(p.sigma)
+    for k in range(3):
+        s.bg[k] = float(p.bg[k])
+    s.n = n
+    return s
+
+
+def camera_struct(cam: dict) -> _lib.Camera:
+    c = _lib.Camera()
+    R = np.asarray(cam["R"], dtype=np.float32).reshape(9)
+    t = np.asarray(cam["t"], dtype=np.float32).reshape(3)
+    for k in range(9):
+        c.R[k] = float(R[k])
+    for k in range(3):
+        c.t[k] = float(t[k])
+    c.fx, c.fy, c.cx, c.cy = (float(cam["fx"]), float(cam["fy"]), float(cam["cx"]), float(cam["cy"]))
+    c.width, c.height = int(cam["width"]), int(cam["height"])
+    return c
+
+
+class _DeviceArray:
+    """Zero-copy view of library-owned device memory through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = dict(shape=tuple(shape), typestr=typestr, data=(int(ptr), False),
+                                             version=3, strides=None)
+
+
+def _stream_ptr(stream: Optional[torch.cuda.Stream] = None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Renderer:
+    """A SparseOIT context: active set, per-view frozen sums, batched fwd / bwd."""
+
+    def __init__(self, n_splats: int, view_sizes: Sequence[Sequence[int]], max_pairs: int = 0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("sparseoit needs a CUDA device")
+        self.lib = _lib.load()
+        self.n = int(n_splats)
+        self.view_sizes = [(int(w), int(h)) for (w, h) in view_sizes]
+        nv = len(self.view_sizes)
+        ws = (ctypes.c_int32 * nv)(*[w for w, _ in self.view_sizes])
+        hs = (ctypes.c_int32 * nv)(*[h for _, h in self.view_sizes])
+        cfg = _lib.Config()
+        cfg.max_pairs = int(max_pairs)
+        self._ctx = ctypes.c_void_p()
+        rc = self.lib.sparseoit_create(ctypes.byref(self._ctx), self.n, nv, ws, hs, ctypes.byref(cfg))
+        if rc != _lib.OK:
+            raise SparseOITError(rc, self.lib.sparseoit_last_error(None).decode())
+        self.n_active = 0
+        self.forward_id = 0
+        self._last_views: List[int] = []
+        self._keep = None
+
+    # ------------------------------------------------------------ basics
+    def _check(self, rc):
+        if rc != _lib.OK:
+            raise SparseOITError(rc, self.lib.sparseoit_last_error(self._ctx).decode())
+
+    def close(self):
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            self.lib.sparseoit_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -------------------------------------------------------- active set
+    def set_active(self, mask: torch.Tensor, stream=None):
+        """Sec. 4.1: set A from a [N] bool / uint8 CUDA mask (synchronises)."""
+        if mask.dtype == torch.bool:
+            mask = mask.to(torch.uint8)
+        if mask.dtype != torch.uint8 or not mask.is_cuda or mask.numel() != self.n:
+            raise ValueError("mask must be a CUDA uint8/bool tensor of n_splats entries")
+        mask = mask.contiguous()
+        self._check(self.lib.sparseoit_set_active(self._ctx, ctypes.c_void_p(mask.data_ptr()), self.n,
+                                                  ctypes.c_void_p(_stream_ptr(stream))))
+        p, na = ctypes.c_void_p(), ctypes.c_int64()
+        self._check(self.lib.sparseoit_get_active(self._ctx, ctypes.byref(p), ctypes.byref(na)))
+        self.n_active = int(na.value)
+
+    def active_indices(self) -> torch.Tensor:
+        """Ascending int32 indices of A (a copy)."""
+        p, na = ctypes.c_void_p(), ctypes.c_int64()
+        self._check(self.lib.sparseoit_get_active(self._ctx, ctypes.byref(p), ctypes.byref(na)))
+        if na.value == 0:
+            return torch.zeros(0, dtype=torch.int32, device="cuda")
+        return torch.as_tensor(_DeviceArray(p.value, (na.value,), "<i4"), device="cuda").clone()
+
+    def frozen_sums(self, view: int) -> torch.Tensor:
+        """[5, H, W] frozen sums (P_r, P_g, P_b, Q, log T) of a view (a copy)."""
+        p = ctypes.c_void_p()
+        self._check(self.lib.sparseoit_get_frozen(self._ctx, int(view), ctypes.byref(p)))
+        W, H = self.view_sizes[view]
+        return torch.as_tensor(_DeviceArray(p.value, (5, H, W), "<f4"), device="cuda").clone()
+
+    def commit_frozen(self, splats: SplatParams, cam: dict, view: int, mode: str = "incremental", stream=None):
+        """Sec. 4.1 / Alg. 2 BAU: bring the view's frozen sums up to date."""
+        m = _lib.COMMIT_INCREMENTAL if mode == "incremental" else _lib.COMMIT_RECOMPUTE
+        s = splats_struct(splats)
+        c = camera_struct(cam)
+        self._check(self.lib.sparseoit_commit_frozen(self._ctx, ctypes.byref(s), ctypes.byref(c), int(view), m,
+                                                     ctypes.c_void_p(_stream_ptr(stream))))
+
+    # ------------------------------------------------------ forward / bwd
+    def forward(self, splats: SplatParams, cams: Sequence[dict], views: Sequence[int],
+                targets: Optional[Sequence[torch.Tensor]] = None, stream=None, images=None, loss=None):
+        """Render the active set of the given views (Eq. 7 with the frozen sums).
+
+        Returns (images list of [H, W, 3], loss tensor [1] or None)."""
+        nv = len(views)
+        if nv != len(cams) or nv < 1 or nv > _lib.MAX_BATCH_VIEWS:
+            raise ValueError("need 1..32 views, one camera each")
+        s = splats_struct(splats)
+        camarr = (_lib.Camera * nv)(*[camera_struct(c) for c in cams])
+        varr = (ctypes.c_int32 * nv)(*[int(v) for v in views])
+        if images is None:
+            images = [torch.empty((self.view_sizes[v][1], self.view_sizes[v][0], 3), dtype=torch.float32,
+                                  device="cuda") for v in views]
+        iptr = (ctypes.c_void_p * nv)(*[im.data_ptr() for im in images])
+        tptr = None
+        if targets is not None:
+            for tg, v in zip(targets, views):
+                W, H = self.view_sizes[v]
+                if tuple(tg.shape) != (H, W, 3) or tg.dtype != torch.float32 or not tg.is_cuda \
+                        or not tg.is_contiguous():
+                    raise ValueError("targets must be contiguous float32 CUDA [H, W, 3]")
+            tptr = (ctypes.c_void_p * nv)(*[tg.data_ptr() for tg in targets])
+            if loss is None:
+                loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        self._check(self.lib.sparseoit_forward(self._ctx, ctypes.byref(s), camarr, varr, nv, iptr, tptr,
+                                               ctypes.c_void_p(loss.data_ptr() if loss is not None else 0),
+                                               ctypes.c_void_p(_stream_ptr(stream))))
+        self.forward_id += 1
+        self._last_views = list(views)
+        self._keep = (images, targets, loss)
+        return images, loss
+
+    def backward(self, splats: SplatParams, grad_images: Optional[Sequence[torch.Tensor]] = None,
+                 rows_by_splat: bool = False, stream=None, out: Optional[Dict[str, torch.Tensor]] = None):
+        """Gradients of the last forward's loss for the active splats (App. B).
+
+        rows_by_splat=False: compact [n_active, ...] rows in active-index order;
+        True: full [N, ...] arrays, inactive rows zero."""
+        s = splats_struct(splats)
+        rows = self.n if rows_by_splat else self.n_active
+        if out is None:
+            alloc = torch.zeros if rows_by_splat else torch.empty
+            out = {name: alloc((rows,) + PARAM_SHAPES[name], dtype=torch.float32, device="cuda")
+                   for name in PARAM_NAMES}
+            out["sigma"] = torch.empty(1, dtype=torch.float32, device="cuda")
+        g = _lib.Grads()
+        for name in PARAM_NAMES + ("sigma",):
+            setattr(g, name, out[name].data_ptr())
+        g.rows_by_splat = 1 if rows_by_splat else 0
+        gptr = None
+        if grad_images is not None:
+            gi = [x.contiguous().float() for x in grad_images]
+            gptr = (ctypes.c_void_p * len(gi))(*[x.data_ptr() for x in gi])
+            self._keep_grad = gi
+        self._check(self.lib.sparseoit_backward(self._ctx, ctypes.byref(s), gptr, ctypes.byref(g),
+                                                ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    # ------------------------------------------------------------ misc
+    def status(self, stream=None):
+        self._check(self.lib.sparseoit_status(self._ctx, ctypes.c_void_p(_stream_ptr(stream))))
+
+    def set_counting(self, enable: bool):
+        self._check(self.lib.sparseoit_set_counting(self._ctx, 1 if enable else 0))
+
+    def last_counts(self, stream=None):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.sparseoit_last_counts(self._ctx, ctypes.c_void_p(_stream_ptr(stream)),
+                                                   ctypes.byref(a), ctypes.byref(b)))
+        return int(a.value), int(b.value)
+
+    def reserve_pairs(self, max_pairs: int):
+        self._check(self.lib.sparseoit_reserve_pairs(self._ctx, int(max_pairs)))
+
+
+class SparseOITRender(torch.autograd.Function):
+    """Autograd wrapper: images of the active set; gradients for all rows
+    (inactive rows zero), computed by sparseoit_backward."""
+
+    @staticmethod
+    def forward(ctx, renderer: Renderer, cams, views, sigma: float, bg, means, quats, log_scales, opacity_logits,
+                sh_color, sh_weight):
+        sp = SplatParams(means.detach(), quats.detach(), log_scales.detach(), opacity_logits.detach(),
+                         sh_color.detach(), sh_weight.detach(), float(sigma), tuple(bg))
+        images, _ = renderer.forward(sp, cams, views)
+        ctx.renderer = renderer
+        ctx.splats = sp
+        ctx.forward_id = renderer.forward_id
+        ctx.shapes = [tuple(im.shape) for im in images]
+        return tuple(images)
+
+    @staticmethod
+    def backward(ctx, *grad_images):
+        r: Renderer = ctx.renderer
+        if r.forward_id != ctx.forward_id:
+            raise RuntimeError("SparseOITRender.backward: another forward ran on this renderer since")
+        gi = [g if g is not None else torch.zeros(shp, dtype=torch.float32, device="cuda")
+              for g, shp in zip(grad_images, ctx.shapes)]
+        grads = r.backward(ctx.splats, gi, rows_by_splat=True)
+        sh_dt = ctx.splats.sh_color.dtype
+        return (None, None, None, None, None, grads["means"], grads["quats"], grads["log_scales"],
+                grads["opacity_logits"], grads["sh_color"].to(sh_dt), grads["sh_weight"].to(sh_dt))
