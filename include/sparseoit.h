@@ -204,6 +204,23 @@ int sparseoit_last_counts(sparseoit_ctx *ctx, void *stream, int64_t *n_pairs, in
  * raster (off by default; costs one atomic per thread block). */
 int sparseoit_set_counting(sparseoit_ctx *ctx, int32_t enable);
 
+/* Per-kernel device time, accumulated while profiling is enabled. */
+typedef struct {
+    char name[32];          /* kernel name                                   */
+    int64_t launches;       /* launches timed since the last get_profile     */
+    double total_ms;        /* summed CUDA-event durations of those launches */
+} sparseoit_kernel_time;
+
+/* Enable (1) / disable (0) profiling: every kernel launch of the library is
+ * bracketed by CUDA events recorded on the launching stream.  Must be off
+ * while a stream is being captured into a CUDA graph. */
+int sparseoit_set_profiling(sparseoit_ctx *ctx, int32_t enable);
+
+/* Synchronise on the recorded events and return the per-kernel totals since
+ * the previous call (then reset).  Writes at most max_entries entries to out
+ * (host array) and their number to *n_out. */
+int sparseoit_get_profile(sparseoit_ctx *ctx, int32_t max_entries, sparseoit_kernel_time *out, int32_t *n_out);
+
 /* Last error message of the context (or of the last failed create when ctx
  * is NULL).  Never NULL. */
 const char *sparseoit_last_error(const sparseoit_ctx *ctx);

@@ -182,10 +182,11 @@ def render(scene, cam, subset=None, frozen_sums=None, brute=False, window=None, 
     return dict(image=img, sums=sums, aux=aux, amb=amb, pairs=pairs, clamped=clamped)
 
 
-def backward(scene, cam, sums_total, dL_dC, active=None, window=None, amb_band=0.0):
+def backward(scene, cam, sums_total, dL_dC, active=None, window=None, amb_band=0.0, with_scale=False):
     """Analytic gradient of L = sum dL_dC . C (Eq. 10 chained to all parameters).
 
-    Returns (grads [N,75] with unselected rows NaN, dL/dsigma, amb_splat [N] uint8).
+    Returns (grads [N,75] with unselected rows NaN, dL/dsigma, amb_splat [N] uint8), and with
+    with_scale=True a fourth value: the sum of |per-splat dL/dsigma terms|.
     """
     lib = _load()
     n, a = _splat_args(scene)
@@ -193,7 +194,7 @@ def backward(scene, cam, sums_total, dL_dC, active=None, window=None, amb_band=0
     s = _f64(sums_total).reshape(5, H, W)
     g = _f64(dL_dC).reshape(H, W, 3)
     grads = np.full((n, NPARAM), np.nan)
-    dsig = np.zeros(1)
+    dsig = np.zeros(2)
     amb = np.zeros(n, dtype=np.uint8)
     m = _mask(active, n)
     win = _window(window)
@@ -202,4 +203,6 @@ def backward(scene, cam, sums_total, dL_dC, active=None, window=None, amb_band=0
     lib.oracle_backward(n, *[_ptr(x) for x in a], float(scene["sigma"]), _ptr(b), _ptr(c), W, H,
                         _ptr(m, _u8p), _ptr(s), _ptr(g), _ptr(win, _ip), float(amb_band),
                         _ptr(grads), _ptr(dsig), _ptr(amb, _u8p))
+    if with_scale:
+        return grads, float(dsig[0]), amb, float(dsig[1])
     return grads, float(dsig[0]), amb

@@ -449,7 +449,9 @@ int oracle_compose(int W, int H, const double *sums, const double *bg, double *i
  * grads[n, 75] rows of selected splats are overwritten, the others are not
  * touched.  Row layout: mean (3), quaternion (4), log-scale (3),
  * opacity logit (1), colour SH [16][3] (48), weight SH (16).
- * dsigma (optional) = dL/dsigma summed over the selected splats.
+ * dsigma (optional, [2]) = dL/dsigma summed over the selected splats and
+ * the sum of the absolute values of those per-splat terms (the scale a
+ * rounding error of the sum is measured against).
  * amb_splat (optional, [n]) is set to 1 for a selected splat that has a pair
  * whose unclamped alpha is within exp(amb_band) of 1/255 or of 0.99, a
  * colour / weight SH value within amb_band of the max(0,.) kink, or
@@ -471,9 +473,9 @@ int oracle_backward(int64_t n, const double *means, const double *quats, const d
     int wx0, wy0, wx1, wy1;
     clip_window(window, W, H, &wx0, &wy0, &wx1, &wy1);
     double slack = (amb_band > 1e-6 ? amb_band : 1e-6) + 1e-9;
-    double dsig_total = 0.0;
+    double dsig_total = 0.0, dsig_abs = 0.0;
 
-#pragma omp parallel for schedule(dynamic, 64) reduction(+ : dsig_total)
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : dsig_total, dsig_abs)
     for (int64_t i = 0; i < n; ++i) {
         if (active && !active[i]) continue;
         double *gout = grads + (int64_t)OR_NPARAM * i;
@@ -584,6 +586,7 @@ int oracle_backward(int64_t n, const double *means, const double *quats, const d
             g_v = g_w * P.zterm;
             gt[2] += g_w * P.v * (-1.0 / sigma);
             dsig_total += g_w * P.v * z / (sigma * sigma);
+            dsig_abs += fabs(g_w * P.v * z / (sigma * sigma));
         }
         /* Eq. 4 colour and weight SH */
         double Yb[16], dY[48];
@@ -656,7 +659,7 @@ int oracle_backward(int64_t n, const double *means, const double *quats, const d
         double qdot = qa * gq[0] + qb * gq[1] + qc * gq[2] + qd * gq[3];
         for (int k = 0; k < 4; ++k) gout[3 + k] = (gq[k] - P.qn[k] * qdot) / P.qlen;
     }
-    if (dsigma) *dsigma = dsig_total;
+    if (dsigma) { dsigma[0] = dsig_total; dsigma[1] = dsig_abs; }
     return 0;
 }
 

@@ -33,7 +33,7 @@ EXPORTED = (
     "sparseoit_create", "sparseoit_destroy", "sparseoit_set_active", "sparseoit_get_active",
     "sparseoit_commit_frozen", "sparseoit_get_frozen", "sparseoit_forward", "sparseoit_backward",
     "sparseoit_reserve_pairs", "sparseoit_status", "sparseoit_last_counts", "sparseoit_set_counting",
-    "sparseoit_last_error", "sparseoit_version",
+    "sparseoit_set_profiling", "sparseoit_get_profile", "sparseoit_last_error", "sparseoit_version",
 )
 
 
@@ -54,6 +54,10 @@ class Grads(ctypes.Structure):
     _fields_ = [("means", ctypes.c_void_p), ("quats", ctypes.c_void_p), ("log_scales", ctypes.c_void_p),
                 ("opacity_logits", ctypes.c_void_p), ("sh_color", ctypes.c_void_p), ("sh_weight", ctypes.c_void_p),
                 ("sigma", ctypes.c_void_p), ("rows_by_splat", ctypes.c_int32)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
 class Config(ctypes.Structure):
@@ -90,6 +94,8 @@ def load(path: str = LIB_PATH):
             "sparseoit_status": ([vp, vp], ctypes.c_int),
             "sparseoit_last_counts": ([vp, vp, P(i64), P(i64)], ctypes.c_int),
             "sparseoit_set_counting": ([vp, i32], ctypes.c_int),
+            "sparseoit_set_profiling": ([vp, i32], ctypes.c_int),
+            "sparseoit_get_profile": ([vp, i32, P(KernelTime), P(i32)], ctypes.c_int),
             "sparseoit_last_error": ([vp], ctypes.c_char_p),
             "sparseoit_version": ([], ctypes.c_int),
         }

@@ -7,6 +7,7 @@
 // offsets, the pair arena, the pixel states and the screen-space gradients.
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -51,6 +52,12 @@ struct sparseoit_ctx {
     unsigned long long *d_contrib = nullptr;
     bool counting = false;
 
+    // profiling: events bracketing every launch while enabled
+    bool profiling = false;
+    struct Mark { const char *name; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> event_pool;
+
     // last forward
     bool have_fwd = false;
     bool last_fused = false;
@@ -71,6 +78,38 @@ static int cuda_check(sparseoit_ctx *c, cudaError_t e, const char *what) {
     const int code = (e == cudaErrorMemoryAllocation) ? SPARSEOIT_ERR_OOM : SPARSEOIT_ERR_CUDA;
     return fail(c, code, std::string(what) + ": " + cudaGetErrorString(e));
 }
+
+static cudaEvent_t take_event(sparseoit_ctx *ctx) {
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Brackets one kernel launch with events on its stream when profiling.
+struct ProfScope {
+    sparseoit_ctx *ctx;
+    const char *name;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    ProfScope(sparseoit_ctx *c, const char *n, cudaStream_t s) : ctx(c), name(n), st(s) {
+        if (ctx->profiling) {
+            a = take_event(ctx);
+            if (a) cudaEventRecord(a, st);
+        }
+    }
+    ~ProfScope() {
+        if (!a) return;
+        cudaEvent_t b = take_event(ctx);
+        if (!b) { ctx->event_pool.push_back(a); return; }
+        cudaEventRecord(b, st);
+        ctx->marks.push_back({name, a, b});
+    }
+};
 
 #define CK(call, what)                                              \
     do {                                                            \
@@ -149,13 +188,22 @@ static int render_pass_bin(sparseoit_ctx *ctx, Batch &b, const sparseoit_splats 
         return fail(ctx, SPARSEOIT_ERR_STATE, "batch workspace not sized");
     CK(cudaMemsetAsync(ctx->d_tile_count, 0, (size_t)b.total_tiles * sizeof(int), st), "memset(tile counts)");
     const SplatPtrs sp = splat_ptrs(s);
-    launch_project(b, sp, s->sh_dtype == SPARSEOIT_BF16, list1, n1, list2, n2, ctx->d_rec, ctx->d_ext,
-                   ctx->d_tile_count, st);
+    {
+        ProfScope ps(ctx, "project", st);
+        launch_project(b, sp, s->sh_dtype == SPARSEOIT_BF16, list1, n1, list2, n2, ctx->d_rec, ctx->d_ext,
+                       ctx->d_tile_count, st);
+    }
     CK_LAUNCH("project_kernel");
-    launch_scan_tiles(ctx->d_tile_count, b.total_tiles, ctx->d_offsets, ctx->d_cursor, ctx->pair_cap, ctx->d_status,
-                      ctx->d_npairs, st);
+    {
+        ProfScope ps(ctx, "scan_tiles", st);
+        launch_scan_tiles(ctx->d_tile_count, b.total_tiles, ctx->d_offsets, ctx->d_cursor, ctx->pair_cap,
+                          ctx->d_status, ctx->d_npairs, st);
+    }
     CK_LAUNCH("scan_tiles_kernel");
-    launch_scatter(b, ctx->d_rec, ctx->d_ext, ctx->d_cursor, ctx->d_pairs, ctx->pair_cap, st);
+    {
+        ProfScope ps(ctx, "scatter", st);
+        launch_scatter(b, ctx->d_rec, ctx->d_ext, ctx->d_cursor, ctx->d_pairs, ctx->pair_cap, st);
+    }
     CK_LAUNCH("scatter_kernel");
     return SPARSEOIT_OK;
 }
@@ -265,6 +313,8 @@ int sparseoit_destroy(sparseoit_ctx *ctx) {
                     ctx->d_contrib};
     for (void *p : bufs) if (p) cudaFree(p);
     if (ctx->h_totals) cudaFreeHost(ctx->h_totals);
+    for (auto &m : ctx->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     delete ctx;
     return SPARSEOIT_OK;
 }
@@ -276,8 +326,11 @@ int sparseoit_set_active(sparseoit_ctx *ctx, const uint8_t *d_mask, int64_t n, v
     cudaStream_t st = (cudaStream_t)stream;
     const uint8_t *prev = ctx->have_mask ? ctx->d_mask[ctx->cur] : nullptr;
     uint8_t *store = ctx->d_mask[ctx->cur ^ 1];
-    launch_compact(d_mask, prev, n, ctx->d_blk, ctx->d_totals, ctx->d_idx_active, ctx->d_idx_comp, ctx->d_idx_plus,
-                   ctx->d_idx_minus, store, st);
+    {
+        ProfScope ps(ctx, "compact", st);
+        launch_compact(d_mask, prev, n, ctx->d_blk, ctx->d_totals, ctx->d_idx_active, ctx->d_idx_comp,
+                       ctx->d_idx_plus, ctx->d_idx_minus, store, st);
+    }
     CK_LAUNCH("compaction kernels");
     CK(cudaMemcpyAsync(ctx->h_totals, ctx->d_totals, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, st),
        "copy active counts");
@@ -343,6 +396,7 @@ int sparseoit_commit_frozen(sparseoit_ctx *ctx, const sparseoit_splats *splats, 
         if (rc) return rc;
         rc = render_pass_bin(ctx, b, splats, l1, (int)n1, l2, (int)n2, st);
         if (rc) return rc;
+        ProfScope ps(ctx, "raster_sums", st);
         launch_raster_fwd(b, kRasterSums, ctx->d_rec, ctx->d_offsets, ctx->d_pairs, ctx->pair_cap, splats->bg, nullptr,
                           nullptr, st);
         CK_LAUNCH("raster_fwd_kernel(sums)");
@@ -398,9 +452,12 @@ int sparseoit_forward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const 
     if (ctx->counting) CK(cudaMemsetAsync(ctx->d_contrib, 0, sizeof(unsigned long long), st), "memset(counter)");
     rc = render_pass_bin(ctx, b, splats, ctx->d_idx_active, (int)ctx->n_active, nullptr, 0, st);
     if (rc) return rc;
-    launch_raster_fwd(b, d_targets ? kRasterFused : kRasterAux, ctx->d_rec, ctx->d_offsets, ctx->d_pairs,
-                      ctx->pair_cap, splats->bg, d_targets ? d_loss : nullptr, ctx->counting ? ctx->d_contrib : nullptr,
-                      st);
+    {
+        ProfScope ps(ctx, "raster_fwd", st);
+        launch_raster_fwd(b, d_targets ? kRasterFused : kRasterAux, ctx->d_rec, ctx->d_offsets, ctx->d_pairs,
+                          ctx->pair_cap, splats->bg, d_targets ? d_loss : nullptr,
+                          ctx->counting ? ctx->d_contrib : nullptr, st);
+    }
     CK_LAUNCH("raster_fwd_kernel");
     ctx->have_fwd = true;
     ctx->last_fused = d_targets != nullptr;
@@ -430,19 +487,26 @@ int sparseoit_backward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const
             if (!d_grad_images[k]) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "grad image pointer is null");
             b.v[k].grad_image = d_grad_images[k];
         }
+        ProfScope ps(ctx, "prep_state", st);
         launch_prep_state(b, splats->bg, st);
         CK_LAUNCH("prep_state_kernel");
     }
     const int64_t nrec = (int64_t)b.n_views * ctx->last_n_list;
     CK(grow(&ctx->d_sgrad, &ctx->sgrad_cap, 3 * nrec), "cudaMalloc(screen grads)");
     CK(cudaMemsetAsync(ctx->d_sgrad, 0, (size_t)(3 * nrec) * sizeof(float4), st), "memset(screen grads)");
-    launch_raster_bwd(b, ctx->d_rec, ctx->d_offsets, ctx->d_pairs, ctx->pair_cap, ctx->d_sgrad, st);
+    {
+        ProfScope ps(ctx, "raster_bwd", st);
+        launch_raster_bwd(b, ctx->d_rec, ctx->d_offsets, ctx->d_pairs, ctx->pair_cap, ctx->d_sgrad, st);
+    }
     CK_LAUNCH("raster_bwd_kernel");
     CK(cudaMemsetAsync(out->sigma, 0, sizeof(float), st), "memset(dsigma)");
     GradPtrs g{out->means,    out->quats,     out->log_scales, out->opacity_logits,
                out->sh_color, out->sh_weight, out->sigma,      out->rows_by_splat != 0};
-    launch_project_bwd(b, splat_ptrs(splats), splats->sh_dtype == SPARSEOIT_BF16, ctx->d_idx_active, ctx->last_n_list,
-                       ctx->d_sgrad, g, st);
+    {
+        ProfScope ps(ctx, "project_bwd", st);
+        launch_project_bwd(b, splat_ptrs(splats), splats->sh_dtype == SPARSEOIT_BF16, ctx->d_idx_active,
+                           ctx->last_n_list, ctx->d_sgrad, g, st);
+    }
     CK_LAUNCH("project_bwd_kernel");
     return SPARSEOIT_OK;
 }
@@ -485,6 +549,39 @@ int sparseoit_last_counts(sparseoit_ctx *ctx, void *stream, int64_t *n_pairs, in
     CK(cudaStreamSynchronize(st), "counts sync");
     if (n_pairs) *n_pairs = hp;
     if (n_contrib) *n_contrib = (int64_t)hc;
+    return SPARSEOIT_OK;
+}
+
+int sparseoit_set_profiling(sparseoit_ctx *ctx, int32_t enable) {
+    if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
+    ctx->profiling = enable != 0;
+    return SPARSEOIT_OK;
+}
+
+int sparseoit_get_profile(sparseoit_ctx *ctx, int32_t max_entries, sparseoit_kernel_time *out, int32_t *n_out) {
+    if (!ctx || !n_out || (max_entries > 0 && !out)) return SPARSEOIT_ERR_INVALID_ARG;
+    std::map<std::string, std::pair<int64_t, double>> acc;
+    for (auto &m : ctx->marks) {
+        CK(cudaEventSynchronize(m.b), "profile sync");
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, m.a, m.b), "profile elapsed");
+        auto &e = acc[m.name];
+        e.first += 1;
+        e.second += ms;
+        ctx->event_pool.push_back(m.a);
+        ctx->event_pool.push_back(m.b);
+    }
+    ctx->marks.clear();
+    int k = 0;
+    for (auto &kv : acc) {
+        if (k >= max_entries) break;
+        memset(out[k].name, 0, sizeof(out[k].name));
+        strncpy(out[k].name, kv.first.c_str(), sizeof(out[k].name) - 1);
+        out[k].launches = kv.second.first;
+        out[k].total_ms = kv.second.second;
+        ++k;
+    }
+    *n_out = k;
     return SPARSEOIT_OK;
 }
 

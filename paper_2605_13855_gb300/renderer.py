@@ -257,6 +257,16 @@ class Renderer:
                                                    ctypes.byref(a), ctypes.byref(b)))
         return int(a.value), int(b.value)
 
+    def set_profiling(self, enable: bool):
+        self._check(self.lib.sparseoit_set_profiling(self._ctx, 1 if enable else 0))
+
+    def get_profile(self) -> Dict[str, tuple]:
+        """{kernel: (launches, total_ms)} since the previous call (synchronises)."""
+        buf = (_lib.KernelTime * 32)()
+        n = ctypes.c_int32()
+        self._check(self.lib.sparseoit_get_profile(self._ctx, 32, buf, ctypes.byref(n)))
+        return {buf[k].name.decode(): (int(buf[k].launches), float(buf[k].total_ms)) for k in range(n.value)}
+
     def reserve_pairs(self, max_pairs: int):
         self._check(self.lib.sparseoit_reserve_pairs(self._ctx, int(max_pairs)))
 

@@ -56,13 +56,14 @@ PROBE = r"""
 #include "sparseoit.h"
 #define F(T, m) printf(#T "." #m " %zu\n", offsetof(T, m));
 int main(void) {
-  printf("camera %zu\nsplats %zu\ngrads %zu\nconfig %zu\n", sizeof(sparseoit_camera), sizeof(sparseoit_splats),
-         sizeof(sparseoit_grads), sizeof(sparseoit_config));
+  printf("camera %zu\nsplats %zu\ngrads %zu\nconfig %zu\nktime %zu\n", sizeof(sparseoit_camera),
+         sizeof(sparseoit_splats), sizeof(sparseoit_grads), sizeof(sparseoit_config), sizeof(sparseoit_kernel_time));
   F(sparseoit_camera, fx) F(sparseoit_camera, width) F(sparseoit_camera, height)
   F(sparseoit_splats, sh_color) F(sparseoit_splats, sh_dtype) F(sparseoit_splats, sigma) F(sparseoit_splats, bg)
   F(sparseoit_splats, n)
   F(sparseoit_grads, sigma) F(sparseoit_grads, rows_by_splat)
   F(sparseoit_config, max_pairs) F(sparseoit_config, reserved)
+  F(sparseoit_kernel_time, launches) F(sparseoit_kernel_time, total_ms)
   return 0;
 }
 """
@@ -80,8 +81,9 @@ def test_ctypes_structs_match_header(tmp_path):
     assert got["splats"] == ctypes.sizeof(_lib.Splats)
     assert got["grads"] == ctypes.sizeof(_lib.Grads)
     assert got["config"] == ctypes.sizeof(_lib.Config)
+    assert got["ktime"] == ctypes.sizeof(_lib.KernelTime)
     pairs = {"sparseoit_camera": _lib.Camera, "sparseoit_splats": _lib.Splats, "sparseoit_grads": _lib.Grads,
-             "sparseoit_config": _lib.Config}
+             "sparseoit_config": _lib.Config, "sparseoit_kernel_time": _lib.KernelTime}
     for key, off in got.items():
         if "." not in key:
             continue

@@ -7,7 +7,7 @@ import oracle
 from paper_2605_13855_gb300 import scenes
 from paper_2605_13855_gb300._lib import ERR_CAPACITY, ERR_STATE, SparseOITError
 from paper_2605_13855_gb300.renderer import Renderer, SparseOITRender, SplatParams
-from tests.parity_util import AMB_BAND, GRAD_TOL, IMG_TOL, assert_grads_close, image_error, to_np
+from tests.parity_util import AMB_BAND, AMB_PIX_MAX, GRAD_TOL, IMG_TOL, assert_grads_close, image_error, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -45,15 +45,19 @@ def _check_view(r, sp, scene, cam, view, mask, seed, check_grads=True, window=No
     else:
         e, frac = image_error(img, ref["image"], ref["amb"])
     assert e <= IMG_TOL, f"image rel err {e:.3g}"
-    assert frac <= 2e-3, f"ambiguous pixel fraction {frac:.3g}"
+    assert frac <= AMB_PIX_MAX, f"ambiguous pixel fraction {frac:.3g}"
     if not check_grads:
         return e, None
     act = mask.astype(bool)
-    gref, dsig_ref, amb = oracle.backward(scene, cam, ref["sums"], g, active=act, window=window, amb_band=AMB_BAND)
+    gref, dsig_ref, amb, dsig_scale = oracle.backward(scene, cam, ref["sums"], g, active=act, window=window,
+                                                      amb_band=AMB_BAND, with_scale=True)
     rows = np.where(act)[0]
     keep = amb[rows] == 0
-    assert keep.mean() > 0.97, f"too many ambiguous splats: {1 - keep.mean():.3g}"
-    errs = assert_grads_close(grads, gref, rows, keep, dsig=float(grads["sigma"].item()), dsig_ref=dsig_ref)
+    assert keep.mean() > 0.95, f"too many ambiguous splats: {1 - keep.mean():.3g}"
+    errs = assert_grads_close(grads, gref, rows, keep, dsig=float(grads["sigma"].item()), dsig_ref=dsig_ref,
+                              dsig_scale=dsig_scale)
+    print(f"parity {cam['width']}x{cam['height']}: image {e:.2e} (ambiguous px {frac:.2e}), grads",
+          {k: f"{v:.2e}" for k, v in errs.items()}, f"ambiguous splats {1 - keep.mean():.2e}")
     return e, errs
 
 
@@ -70,23 +74,30 @@ def test_tiny_fused_l1():
     """Fused L1 loss (target = render of a second splat set) against the oracle."""
     scene, tscene, cam = scenes.tiny_workload()
     n = scene["means"].shape[0]
-    target = oracle.render(tscene, cam)["image"].astype(np.float32)
+    ref = oracle.render(scene, cam, amb_band=AMB_BAND)
+    target = oracle.render(tscene, cam)["image"]
+    # Where the target is within 1e-4 of the render (but not equal) the sign of
+    # C - I is decided by rounding; move those target values 1e-4 away so that
+    # FP32 and FP64 take the same L1 sign (exact ties, e.g. empty background
+    # in both, stay ties: sign(0) = 0 on both sides).
+    d = ref["image"] - target
+    near = (np.abs(d) < 1e-4) & (d != 0)
+    target = np.where(near, target - 1e-4 * np.sign(d), target).astype(np.float32)
+    diff = ref["image"] - target.astype(np.float64)
+    assert np.abs(diff)[diff != 0].min() > 5e-5
     mask = np.ones(n, np.uint8)
     r, sp = _renderer_for(scene, [cam], mask)
     tg = torch.as_tensor(target, device="cuda")
     images, loss = r.forward(sp, [cam], [0], targets=[tg])
     grads = r.backward(sp)
-    ref = oracle.render(scene, cam, amb_band=AMB_BAND)
-    diff = ref["image"] - target.astype(np.float64)
     HW = cam["width"] * cam["height"]
     lref = np.abs(diff).mean()
     assert abs(loss.item() - lref) <= 1e-5 * lref
     g = np.sign(diff) / (3 * HW)
-    # a pixel whose sign is ambiguous would flip dL/dC; none expected at this margin
-    assert np.abs(diff)[np.abs(diff) > 0].min() > 1e-5
-    gref, dsig_ref, amb = oracle.backward(scene, cam, ref["sums"], g, amb_band=AMB_BAND)
+    gref, dsig_ref, amb, dsig_scale = oracle.backward(scene, cam, ref["sums"], g, amb_band=AMB_BAND, with_scale=True)
     rows = np.arange(n)
-    assert_grads_close(grads, gref, rows, amb == 0, dsig=float(grads["sigma"].item()), dsig_ref=dsig_ref)
+    assert_grads_close(grads, gref, rows, amb == 0, dsig=float(grads["sigma"].item()), dsig_ref=dsig_ref,
+                       dsig_scale=dsig_scale)
 
 
 @pytest.mark.parametrize("frac", [0.0, 0.1, 1.0])
