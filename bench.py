@@ -116,6 +116,63 @@ def _dist():
     return ws, rank, local
 
 
+def _centred_window(cam, area_px):
+    W, H = cam["width"], cam["height"]
+    a = max(16 * 16, min(area_px, W * H))
+    w = int(min(W, max(16, round((a * W / H) ** 0.5))))
+    h = int(min(H, max(16, round(a / w))))
+    x0, y0 = (W - w) // 2, (H - h) // 2
+    return (x0, y0, x0 + w, y0 + h)
+
+
+def _oracle_step(scene, cam, target, mask, frozen, win):
+    """One fwd+bwd of the active set over the frozen sums, restricted to win, by the FP64 oracle."""
+    import oracle
+    r = oracle.render(scene, cam, subset=mask, frozen_sums=frozen, window=win)
+    diff = r["image"] - target.astype(np.float64)
+    g = np.zeros_like(diff)
+    x0, y0, x1, y1 = win
+    HW = cam["width"] * cam["height"]
+    g[y0:y1, x0:x1] = np.sign(diff[y0:y1, x0:x1]) / (3 * HW)
+    oracle.backward(scene, cam, r["sums"], g, active=mask, window=win)
+    return r["pairs"]
+
+
+def _calibrated_window(scene, cam, target, mask, seconds):
+    """Centred window whose oracle fwd+bwd takes about `seconds` (from a 64x64 probe)."""
+    import oracle
+    area = 64 * 64
+    win = _centred_window(cam, area)
+    for _ in range(4):  # the per-call overhead makes one probe underestimate: refine
+        frozen, _, _ = oracle.render_sums(scene, cam, subset=~mask, window=win)
+        t = time.perf_counter()
+        _oracle_step(scene, cam, target, mask, frozen, win)
+        dt = time.perf_counter() - t
+        if dt >= 0.5 * seconds or (win[2] - win[0]) * (win[3] - win[1]) >= cam["width"] * cam["height"]:
+            break
+        area = int(area * min(64.0, max(1.5, seconds / max(dt, 1e-3))))
+        win = _centred_window(cam, area)
+    return win
+
+
+def _oracle_timing(scene, cam, target, mask, win, steps, warmup):
+    import oracle
+    frozen, _, _ = oracle.render_sums(scene, cam, subset=~mask, window=win)
+    times, evals = [], 0
+    for k in range(warmup + steps):
+        t = time.perf_counter()
+        evals = _oracle_step(scene, cam, target, mask, frozen, win)
+        if k >= warmup:
+            times.append(time.perf_counter() - t)
+    return float(np.mean(times)), evals
+
+
+def _sample_text(win, evals, dt, reps):
+    return (f"fwd+bwd of the 5% active set (all 1M splats given, complement as precomputed sums) on a centred "
+            f"{win[2]-win[0]}x{win[3]-win[1]} px window of the 1297x840 view (E={evals} pairs), FP64, "
+            f"{reps} timed rep(s) of {dt:.2f} s")
+
+
 def run_reference(args):
     """The FP64 oracle timed on the host cores on a bounded sample of the workload."""
     ws, rank, _ = _dist()
@@ -123,73 +180,31 @@ def run_reference(args):
         return
     import oracle
     from paper_2605_13855_gb300 import scenes
-    t0 = time.time()
     scene, cam, target = scenes.unbounded_workload()
     mask = scenes.unbounded_active_mask(scene, HEADLINE_FRACTION).astype(bool)
-    win = _reference_window(cam)
-    # frozen sums of the complement on the window (the pre-render, not timed)
-    frozen, _, _ = oracle.render_sums(scene, cam, subset=~mask, window=win)
-    gen_s = time.time() - t0
-    times, evals = [], 0
-    for step in range(args.warmup + args.steps):
-        t = time.perf_counter()
-        r = oracle.render(scene, cam, subset=mask, frozen_sums=frozen, window=win)
-        diff = r["image"] - target.astype(np.float64)
-        g = np.zeros_like(diff)
-        x0, y0, x1, y1 = win
-        HW = cam["width"] * cam["height"]
-        g[y0:y1, x0:x1] = np.sign(diff[y0:y1, x0:x1]) / (3 * HW)
-        oracle.backward(scene, cam, r["sums"], g, active=mask, window=win)
-        dt = time.perf_counter() - t
-        if step >= args.warmup:
-            times.append(dt)
-            evals = r["pairs"]
-    mean = float(np.mean(times))
+    per_step = min(8.0, 150.0 / max(1, args.steps + args.warmup))
+    win = _calibrated_window(scene, cam, target, mask, per_step)
+    mean, evals = _oracle_timing(scene, cam, target, mask, win, args.steps, args.warmup)
     value = evals / mean
     cores = oracle.num_threads()
-    sample = (f"window {win[2]-win[0]}x{win[3]-win[1]} px at ({win[0]},{win[1]}) of the 1297x840 view, all 1M splats "
-              f"projected, 5% active rendered over the complement's precomputed sums, fwd+bwd, FP64")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + " (oracle on a window sample)", "active_fraction": HEADLINE_FRACTION},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "setup_s": gen_s}
+            "config": {"workload": WORKLOAD + " (FP64 oracle on a window sample)",
+                       "active_fraction": HEADLINE_FRACTION, "window": list(win)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": _sample_text(win, evals, mean, args.steps)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def _reference_window(cam):
-    W, H = cam["width"], cam["height"]
-    w, h = 96, 96
-    x0, y0 = (W - w) // 2, (H - h) // 2
-    return (x0, y0, x0 + w, y0 + h)
-
-
-def cpu_baseline_sample(scene, cam, target, mask, budget_s=12.0):
-    """Oracle fwd+bwd on a centred window sized to take roughly budget_s."""
+def cpu_baseline_sample(scene, cam, target, mask, budget_s=15.0):
+    """The oracle as it stands, timed on the host cores: one fwd+bwd on a window sized to ~budget_s."""
     import oracle
-    win = _reference_window(cam)
-    frozen, _, _ = oracle.render_sums(scene, cam, subset=~mask, window=win)
-    t = time.perf_counter()
-    reps = 0
-    evals = 0
-    while True:
-        r = oracle.render(scene, cam, subset=mask, frozen_sums=frozen, window=win)
-        diff = r["image"] - target.astype(np.float64)
-        g = np.zeros_like(diff)
-        x0, y0, x1, y1 = win
-        HW = cam["width"] * cam["height"]
-        g[y0:y1, x0:x1] = np.sign(diff[y0:y1, x0:x1]) / (3 * HW)
-        oracle.backward(scene, cam, r["sums"], g, active=mask, window=win)
-        reps += 1
-        evals = r["pairs"]
-        if time.perf_counter() - t > budget_s or reps >= 5:
-            break
-    dt = (time.perf_counter() - t) / reps
+    win = _calibrated_window(scene, cam, target, mask, budget_s)
+    dt, evals = _oracle_timing(scene, cam, target, mask, win, 1, 0)
     return {"value": evals / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"fwd+bwd of the 5% active set on a centred {win[2]-win[0]}x{win[3]-win[1]} px window "
-                      f"(E={evals} pairs), FP64, {reps} reps, {dt:.2f} s each"}
+            "sample": _sample_text(win, evals, dt, 1)}
 
 
 def main():
@@ -201,6 +216,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--quick", action="store_true", help="smaller scene (debug only)")
+    ap.add_argument("--fractions", default=None,
+                    help="comma list of active fractions to time (default 0.01,0.05,0.2,1); must include 0.05")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end and stage-update timings")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -311,6 +329,8 @@ def main():
     clock_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
     os.makedirs(os.path.dirname(clock_path), exist_ok=True)
     fr_list = [HEADLINE_FRACTION, 1.0] if args.no_sweep else list(FRACTIONS)
+    if args.fractions:
+        fr_list = sorted({float(x) for x in args.fractions.split(",")} | {HEADLINE_FRACTION})
     with ClockSampler(clock_path) as clk:
         if ws > 1:
             torch.distributed.barrier()
@@ -336,64 +356,67 @@ def main():
         total_E = float(head["E"])
     value = total_E / (ms * 1e-3)
 
-    # active-set update (compaction of a changed mask) and the delayed,
-    # incremental frozen-sum update it implies
-    with torch.cuda.stream(stream):
-        r.set_active(make(HEADLINE_FRACTION), stream=stream)
-        r.commit_frozen(sp, cam, 0, mode="recompute", stream=stream)
-        m2 = make(HEADLINE_FRACTION, seed_shift=1)
-        stream.synchronize()
-        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        a.record(stream)
-        r.set_active(m2, stream=stream)
-        b.record(stream)
-        r.commit_frozen(sp, cam, 0, mode="incremental", stream=stream)
-        c.record(stream)
-        stream.synchronize()
-        set_active_ms, commit_inc_ms = a.elapsed_time(b), b.elapsed_time(c)
-
-    # end to end through the public API with host buffers: every step copies
-    # the full parameter arrays and the target from pinned host memory and
-    # reads back the compact gradients and the loss
-    host = {k: getattr(sp, k).cpu().pin_memory() for k in
-            ("means", "quats", "log_scales", "opacity_logits", "sh_color", "sh_weight")}
-    host_target = target.cpu().pin_memory()
-    with torch.cuda.stream(stream):
-        r.set_active(make(HEADLINE_FRACTION), stream=stream)
-        r.commit_frozen(sp, cam, 0, mode="recompute", stream=stream)
-        out = grads_for(r.n_active)
-        host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
-        host_loss = torch.empty(1).pin_memory()
-        h2d = sum(v.numel() * v.element_size() for v in host.values()) + host_target.numel() * 4
-        d2h = sum(v.numel() * v.element_size() for v in out.values()) + 4
-
-        def e2e_step():
-            for k, v in host.items():
-                getattr(sp, k).copy_(v, non_blocking=True)
-            target.copy_(host_target, non_blocking=True)
-            step(out)
-            for k, v in out.items():
-                host_out[k].copy_(v, non_blocking=True)
-            host_loss.copy_(loss, non_blocking=True)
-
-        for _ in range(args.warmup):
-            e2e_step()
-        stream.synchronize()
-        e_times = []
-        for _ in range(args.steps):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            e2e_step()
-            b.record(stream)
+    set_active_ms = commit_inc_ms = None
+    e2e_ms, h2d, d2h = None, 0, 0
+    if not args.no_e2e:
+        # active-set update (compaction of a changed mask) and the delayed,
+        # incremental frozen-sum update it implies
+        with torch.cuda.stream(stream):
+            r.set_active(make(HEADLINE_FRACTION), stream=stream)
+            r.commit_frozen(sp, cam, 0, mode="recompute", stream=stream)
+            m2 = make(HEADLINE_FRACTION, seed_shift=1)
             stream.synchronize()
-            e_times.append(a.elapsed_time(b))
-    e2e_ms = float(np.mean(e_times))
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(stream)
+            r.set_active(m2, stream=stream)
+            b.record(stream)
+            r.commit_frozen(sp, cam, 0, mode="incremental", stream=stream)
+            c.record(stream)
+            stream.synchronize()
+            set_active_ms, commit_inc_ms = a.elapsed_time(b), b.elapsed_time(c)
+
+        # end to end through the public API with host buffers: every step copies
+        # the full parameter arrays and the target from pinned host memory and
+        # reads back the compact gradients and the loss
+        host = {k: getattr(sp, k).cpu().pin_memory() for k in
+                ("means", "quats", "log_scales", "opacity_logits", "sh_color", "sh_weight")}
+        host_target = target.cpu().pin_memory()
+        with torch.cuda.stream(stream):
+            r.set_active(make(HEADLINE_FRACTION), stream=stream)
+            r.commit_frozen(sp, cam, 0, mode="recompute", stream=stream)
+            out = grads_for(r.n_active)
+            host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
+            host_loss = torch.empty(1).pin_memory()
+            h2d = sum(v.numel() * v.element_size() for v in host.values()) + host_target.numel() * 4
+            d2h = sum(v.numel() * v.element_size() for v in out.values()) + 4
+
+            def e2e_step():
+                for k, v in host.items():
+                    getattr(sp, k).copy_(v, non_blocking=True)
+                target.copy_(host_target, non_blocking=True)
+                step(out)
+                for k, v in out.items():
+                    host_out[k].copy_(v, non_blocking=True)
+                host_loss.copy_(loss, non_blocking=True)
+
+            for _ in range(args.warmup):
+                e2e_step()
+            stream.synchronize()
+            e_times = []
+            for _ in range(args.steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                e2e_step()
+                b.record(stream)
+                stream.synchronize()
+                e_times.append(a.elapsed_time(b))
+        e2e_ms = float(np.mean(e_times))
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
 
     if rank != 0:
         if ws > 1:
@@ -443,8 +466,9 @@ def main():
         "per_kernel_ms": per_kernel,
         "roofline": roofline,
         "cpu_baseline": cpu,
-        "e2e": {"value": total_E / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "e2e": None if e2e_ms is None else {
+            "value": total_E / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": gpu_launches,
         "clocks": clocks,
     }
