@@ -228,6 +228,30 @@ const char *sparseoit_last_error(const sparseoit_ctx *ctx);
 /* SPARSEOIT_ABI_VERSION of the loaded library. */
 int sparseoit_version(void);
 
+/* Allocation-free active-index compaction.  The paper has no counterpart:
+ * this entry point serves callers that cannot allocate device memory --
+ * code that must not trigger the device-wide synchronisation that
+ * cudaMalloc / cudaFree imply, plug-ins running inside another runtime that
+ * owns the whole device memory budget, and deployments that forbid
+ * allocation after start-up.  It writes to d_idx (device, int32, room for n
+ * entries) the ascending indices i with d_mask[i] != 0 (d_mask: device, n
+ * bytes) and their number to *d_count (device int64), the same list that
+ * sparseoit_set_active / sparseoit_get_active produce, without a context.
+ * Its block-count scratch is a fixed file-scope device array of
+ * SPARSEOIT_STATIC_MAX_SPLATS / 4096 ints (16 KiB) that every GPU loading the
+ * library keeps until the process exits; it calls no cudaMalloc, cudaFree or
+ * other allocating routine.  n > SPARSEOIT_STATIC_MAX_SPLATS (or a null
+ * pointer) returns SPARSEOIT_ERR_INVALID_ARG without enqueuing work.  All
+ * calls share that scratch, so calls that overlap on the GPU (other streams
+ * or host threads on the same device) race and must be serialised by the
+ * caller; each call writes every scratch slot it reads, so no clearing is
+ * needed.  The first call on a device looks up the scratch address with
+ * cudaGetSymbolAddress for the current device: make it before any stream
+ * capture.  Asynchronous on `stream`. */
+#define SPARSEOIT_STATIC_MAX_SPLATS (16 * 1024 * 1024)
+int sparseoit_compact_active_static(const uint8_t *d_mask, int64_t n, int32_t *d_idx, int64_t *d_count,
+                                    void *stream);
+
 #ifdef __cplusplus
 }
 #endif

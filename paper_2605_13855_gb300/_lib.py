@@ -34,7 +34,9 @@ EXPORTED = (
     "sparseoit_commit_frozen", "sparseoit_get_frozen", "sparseoit_forward", "sparseoit_backward",
     "sparseoit_reserve_pairs", "sparseoit_status", "sparseoit_last_counts", "sparseoit_set_counting",
     "sparseoit_set_profiling", "sparseoit_get_profile", "sparseoit_last_error", "sparseoit_version",
+    "sparseoit_compact_active_static",
 )
+STATIC_MAX_SPLATS = 16 * 1024 * 1024
 
 
 class Camera(ctypes.Structure):
@@ -98,6 +100,7 @@ def load(path: str = LIB_PATH):
             "sparseoit_get_profile": ([vp, i32, P(KernelTime), P(i32)], ctypes.c_int),
             "sparseoit_last_error": ([vp], ctypes.c_char_p),
             "sparseoit_version": ([], ctypes.c_int),
+            "sparseoit_compact_active_static": ([vp, i64, vp, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
