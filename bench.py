@@ -219,6 +219,7 @@ def main():
     ap.add_argument("--fractions", default=None,
                     help="comma list of active fractions to time (default 0.01,0.05,0.2,1); must include 0.05")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end and stage-update timings")
+    ap.add_argument("--fwd-strip", type=int, default=0, help="forward raster pixels per thread (1, 2, 4; 0 = default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -259,7 +260,7 @@ def main():
         m = scenes.proxy_active_mask(scene["means"], fraction, scenes.UNBOUNDED["seed"] + 2 + seed_shift)
         return torch.as_tensor(m, device=dev)
 
-    r = Renderer(n, [(W, H)], max_pairs=1 << 27)
+    r = Renderer(n, [(W, H)], max_pairs=1 << 27, fwd_pixels_per_thread=args.fwd_strip)
     img = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
     loss = torch.empty(1, dtype=torch.float32, device=dev)
 

@@ -108,7 +108,8 @@ typedef struct {
  * rows, an active splat's gradient goes to the row of its splat index and
  * the rows of inactive splats are not written.  FP32 regardless of sh_dtype;
  * quats, sh_color and sh_weight 16-byte aligned.  The active rows (and
- * *sigma) are overwritten by sparseoit_backward. */
+ * *sigma) are overwritten by sparseoit_backward, or added to with
+ * accumulate != 0. */
 typedef struct {
     float *means;           /* [n_active, 3]     */
     float *quats;           /* [n_active, 4]     */
@@ -118,13 +119,17 @@ typedef struct {
     float *sh_weight;       /* [n_active, 16]    */
     float *sigma;           /* [1]: dL/dsigma summed over active splats and views */
     int32_t rows_by_splat;  /* 0: compact rows, else rows indexed by splat index */
+    int32_t accumulate;     /* 0: overwrite the active rows and *sigma; else add to them
+                               (sum the gradients of several backward calls)        */
 } sparseoit_grads;
 
 /* Launch configuration (NULL = defaults). */
 typedef struct {
     int64_t max_pairs;      /* capacity of the (splat, tile) pair arena shared by
                                the views of one call; 0 = 1 << 25               */
-    int32_t bwd_splats_per_warp; /* reserved, 0 = default (32)                */
+    int32_t fwd_pixels_per_thread; /* forward raster: pixels per thread, 1, 2 or 4
+                                      (256 / 128 / 64 threads per 16x16 tile);
+                                      0 = default (4)                          */
     int32_t reserved[5];
 } sparseoit_config;
 

@@ -55,7 +55,7 @@ class Splats(ctypes.Structure):
 class Grads(ctypes.Structure):
     _fields_ = [("means", ctypes.c_void_p), ("quats", ctypes.c_void_p), ("log_scales", ctypes.c_void_p),
                 ("opacity_logits", ctypes.c_void_p), ("sh_color", ctypes.c_void_p), ("sh_weight", ctypes.c_void_p),
-                ("sigma", ctypes.c_void_p), ("rows_by_splat", ctypes.c_int32)]
+                ("sigma", ctypes.c_void_p), ("rows_by_splat", ctypes.c_int32), ("accumulate", ctypes.c_int32)]
 
 
 class KernelTime(ctypes.Structure):
@@ -63,7 +63,7 @@ class KernelTime(ctypes.Structure):
 
 
 class Config(ctypes.Structure):
-    _fields_ = [("max_pairs", ctypes.c_int64), ("bwd_splats_per_warp", ctypes.c_int32),
+    _fields_ = [("max_pairs", ctypes.c_int64), ("fwd_pixels_per_thread", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 5)]
 
 

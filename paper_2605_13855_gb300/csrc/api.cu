@@ -22,6 +22,7 @@ struct sparseoit_ctx {
     int n_views = 0;
     std::vector<int> W, H;
     int64_t pair_cap = 0;
+    int fwd_strip = 4;            // pixels per thread of the forward raster
     std::string err;
 
     // active set
@@ -259,6 +260,14 @@ int sparseoit_create(sparseoit_ctx **out, int64_t max_splats, int32_t n_views, c
     ctx->N = max_splats;
     ctx->n_views = n_views;
     ctx->pair_cap = (cfg && cfg->max_pairs > 0) ? cfg->max_pairs : (int64_t)1 << 25;
+    if (cfg && cfg->fwd_pixels_per_thread != 0) {
+        const int s = cfg->fwd_pixels_per_thread;
+        if (s != 1 && s != 2 && s != 4) {
+            delete ctx;
+            return fail(nullptr, SPARSEOIT_ERR_INVALID_ARG, "fwd_pixels_per_thread must be 1, 2 or 4");
+        }
+        ctx->fwd_strip = s;
+    }
     if (ctx->pair_cap > 0x7fffffffll) ctx->pair_cap = 0x7fffffffll;
     ctx->view_gen.assign(n_views, -1);
     ctx->d_frozen.assign(n_views, nullptr);
@@ -397,7 +406,7 @@ int sparseoit_commit_frozen(sparseoit_ctx *ctx, const sparseoit_splats *splats, 
         rc = render_pass_bin(ctx, b, splats, l1, (int)n1, l2, (int)n2, st);
         if (rc) return rc;
         ProfScope ps(ctx, "raster_sums", st);
-        launch_raster_fwd(b, kRasterSums, ctx->d_rec, ctx->d_offsets, ctx->d_pairs, ctx->pair_cap, splats->bg, nullptr,
+        launch_raster_fwd(b, kRasterSums, ctx->fwd_strip, ctx->d_rec, ctx->d_offsets, ctx->d_pairs, ctx->pair_cap, splats->bg, nullptr,
                           nullptr, st);
         CK_LAUNCH("raster_fwd_kernel(sums)");
     }
@@ -454,7 +463,7 @@ int sparseoit_forward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const 
     if (rc) return rc;
     {
         ProfScope ps(ctx, "raster_fwd", st);
-        launch_raster_fwd(b, d_targets ? kRasterFused : kRasterAux, ctx->d_rec, ctx->d_offsets, ctx->d_pairs,
+        launch_raster_fwd(b, d_targets ? kRasterFused : kRasterAux, ctx->fwd_strip, ctx->d_rec, ctx->d_offsets, ctx->d_pairs,
                           ctx->pair_cap, splats->bg, d_targets ? d_loss : nullptr,
                           ctx->counting ? ctx->d_contrib : nullptr, st);
     }
@@ -499,9 +508,10 @@ int sparseoit_backward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const
         launch_raster_bwd(b, ctx->d_rec, ctx->d_offsets, ctx->d_pairs, ctx->pair_cap, ctx->d_sgrad, st);
     }
     CK_LAUNCH("raster_bwd_kernel");
-    CK(cudaMemsetAsync(out->sigma, 0, sizeof(float), st), "memset(dsigma)");
-    GradPtrs g{out->means,    out->quats,     out->log_scales, out->opacity_logits,
-               out->sh_color, out->sh_weight, out->sigma,      out->rows_by_splat != 0};
+    if (!out->accumulate) CK(cudaMemsetAsync(out->sigma, 0, sizeof(float), st), "memset(dsigma)");
+    GradPtrs g{out->means,    out->quats,     out->log_scales,          out->opacity_logits,
+               out->sh_color, out->sh_weight, out->sigma,               out->rows_by_splat != 0,
+               out->accumulate != 0};
     {
         ProfScope ps(ctx, "project_bwd", st);
         launch_project_bwd(b, splat_ptrs(splats), splats->sh_dtype == SPARSEOIT_BF16, ctx->d_idx_active,

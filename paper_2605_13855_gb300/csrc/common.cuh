@@ -3,8 +3,8 @@
 // Data layout in HBM (one batch = the views of one forward / commit call):
 //   * projected record of list entry r in batch view v: index q = v * n_list + r,
 //       rec[3q+0] = (mu'x, mu'y, r, A2)        quadratic form, see below
-//       rec[3q+1] = (B2, log2 o, w, c_r)
-//       rec[3q+2] = (c_g, c_b, sign, 0)        sign = +1 / -1 (frozen-sum update)
+//       rec[3q+1] = (B2, log2 o, w, yh)        yh = y half-extent of the cutoff ellipse
+//       rec[3q+2] = (c_r, c_g, c_b, sign)      sign = +1 / -1 (frozen-sum update)
 //     ext[q] = (tau2', y half-extent, x half-extent, dy of the x extreme)
 //   * tile bins: one tile id space for all views of the batch (view v owns
 //     [tile_base, tile_base + tiles_x * tiles_y)); offsets[t] .. offsets[t+1]

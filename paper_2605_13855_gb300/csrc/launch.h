@@ -12,8 +12,10 @@ int launch_scatter(const Batch &b, const float4 *rec, const float4 *ext, int *cu
                    cudaStream_t st);
 
 enum RasterMode { kRasterFused = 0, kRasterAux = 1, kRasterSums = 2 };
-int launch_raster_fwd(const Batch &b, int mode, const float4 *rec, const int *offsets, const uint32_t *pairs,
-                      int64_t cap, const float bg[3], float *loss, unsigned long long *contrib, cudaStream_t st);
+// strip = pixels per thread of the forward raster (1, 2 or 4).
+int launch_raster_fwd(const Batch &b, int mode, int strip, const float4 *rec, const int *offsets,
+                      const uint32_t *pairs, int64_t cap, const float bg[3], float *loss, unsigned long long *contrib,
+                      cudaStream_t st);
 
 int launch_prep_state(const Batch &b, const float bg[3], cudaStream_t st);
 int launch_raster_bwd(const Batch &b, const float4 *rec, const int *offsets, const uint32_t *pairs, int64_t cap,
@@ -22,6 +24,7 @@ int launch_raster_bwd(const Batch &b, const float4 *rec, const int *offsets, con
 struct GradPtrs {
     float *means, *quats, *log_scales, *opacity_logits, *sh_color, *sh_weight, *sigma;
     int rows_by_splat;
+    int accumulate;
 };
 int launch_project_bwd(const Batch &b, const SplatPtrs &sp, bool bf16, const int *list, int n, const float4 *sgrad,
                        GradPtrs out, cudaStream_t st);

@@ -5,49 +5,55 @@
 //
 // Binning is a counting sort: the projection counts, per tile, the splats
 // whose cutoff ellipse {alpha_raw >= 1/255} meets the tile (exact per tile
-// row, see for_each_tile), one exclusive scan over the tiles of the batch
+// row, see row_tiles), one exclusive scan over the tiles of the batch
 // gives the ranges, and a scatter pass appends each splat's record index to
-// every tile it meets.  The order inside a tile is arbitrary: Eq. 7 is a
-// pair of sums and a product, independent of it.
+// every tile it meets (a warp per splat).  The order inside a tile is
+// arbitrary: Eq. 7 is a pair of sums and a product, independent of it.
 #include "common.cuh"
 #include "launch.h"
 
 namespace soit {
 
-// Visit every tile of view vd that the ellipse
-//     (A2 (dx - r dy))^2 + (B2 dy)^2 <= tau2,   (dx, dy) = pixel centre - (mx, my)
-// meets.  e = (tau2, y half-extent, x half-extent, dy at the rightmost point).
-// For the band of pixel-centre rows of a tile row, the x-range of the ellipse
-// is [mx + xl(dL), mx + xr(dR)] where xr(dy) = r dy + sqrt(tau2 - B2^2 dy^2)/A2
-// is concave and peaks at dy = dystar (xl convex, lowest at -dystar), so
-// clamping the peak into the band gives the exact extent of each row.
-template <typename F>
-__device__ __forceinline__ void for_each_tile(const ViewDesc &vd, float mx, float my, float r, float A2, float B2,
-                                              const float4 e, F &&fn) {
-    // Explicitly rounded arithmetic: the count pass and the scatter pass
-    // inline this routine separately and must visit identical tile sets.
-    const float tau2 = e.x, yh = e.y, dys = e.w;
-    if (!(tau2 > 0.f)) return;
+// Tiles of view vd met by the ellipse
+//     (A2 (dx - r dy))^2 + (B2 dy)^2 <= tau2,   (dx, dy) = pixel centre - (mx, my),
+// e = (tau2, y half-extent, x half-extent, dy at the rightmost point).
+// tile_rows gives the tile rows [ty0, ty1]; row_tiles the tile columns
+// [tx0, tx1] of one tile row.  For the band of pixel-centre rows of a tile
+// row, the x-range of the ellipse is [mx + xl(dL), mx + xr(dR)] where
+// xr(dy) = r dy + sqrt(tau2 - B2^2 dy^2)/A2 is concave and peaks at
+// dy = dystar (xl convex, lowest at -dystar), so clamping the peak into the
+// band gives the exact extent of each row.  All arithmetic is explicitly
+// rounded: the count pass and the scatter pass evaluate these separately and
+// must obtain identical tile sets.
+__device__ __forceinline__ bool tile_rows(const ViewDesc &vd, float my, const float4 e, int &ty0, int &ty1) {
+    const float tau2 = e.x, yh = e.y;
+    if (!(tau2 > 0.f)) return false;
     const int py0 = f2i_clamped(ceilf(__fsub_rn(__fsub_rn(my, yh), 0.5f)), 0, vd.H);
     const int py1 = f2i_clamped(floorf(__fsub_rn(__fadd_rn(my, yh), 0.5f)), -1, vd.H - 1);
-    if (py0 > py1) return;
+    if (py0 > py1) return false;
+    ty0 = py0 / kTile;
+    ty1 = py1 / kTile;
+    return true;
+}
+
+__device__ __forceinline__ bool row_tiles(const ViewDesc &vd, float mx, float my, float r, float A2, float B2,
+                                          const float4 e, int ty, int &tx0, int &tx1) {
+    const float tau2 = e.x, yh = e.y, dys = e.w;
+    const float ylo = fmaxf(__fsub_rn((float)(ty * kTile) + 0.5f, my), -yh);
+    const float yhi = fminf(__fsub_rn((float)(ty * kTile + kTile - 1) + 0.5f, my), yh);
+    if (ylo > yhi) return false;
     const float invA2 = __fdiv_rn(1.f, A2), B2sq = __fmul_rn(B2, B2);
-    const int ty0 = py0 / kTile, ty1 = py1 / kTile;
-    for (int ty = ty0; ty <= ty1; ++ty) {
-        const float ylo = fmaxf(__fsub_rn((float)(ty * kTile) + 0.5f, my), -yh);
-        const float yhi = fminf(__fsub_rn((float)(ty * kTile + kTile - 1) + 0.5f, my), yh);
-        if (ylo > yhi) continue;
-        const float dR = fminf(fmaxf(dys, ylo), yhi), dL = fminf(fmaxf(-dys, ylo), yhi);
-        const float hR = __fmul_rn(__fsqrt_rn(fmaxf(__fsub_rn(tau2, __fmul_rn(B2sq, __fmul_rn(dR, dR))), 0.f)), invA2);
-        const float hL = __fmul_rn(__fsqrt_rn(fmaxf(__fsub_rn(tau2, __fmul_rn(B2sq, __fmul_rn(dL, dL))), 0.f)), invA2);
-        const float xr = __fadd_rn(mx, __fadd_rn(__fmul_rn(r, dR), hR));
-        const float xl = __fadd_rn(mx, __fsub_rn(__fmul_rn(r, dL), hL));
-        const int px0 = f2i_clamped(ceilf(__fsub_rn(xl, 0.501f)), 0, vd.W);
-        const int px1 = f2i_clamped(floorf(__fsub_rn(xr, 0.499f)), -1, vd.W - 1);
-        if (px0 > px1) continue;
-        const int row = vd.tile_base + ty * vd.tiles_x;
-        for (int tx = px0 / kTile; tx <= px1 / kTile; ++tx) fn(row + tx);
-    }
+    const float dR = fminf(fmaxf(dys, ylo), yhi), dL = fminf(fmaxf(-dys, ylo), yhi);
+    const float hR = __fmul_rn(__fsqrt_rn(fmaxf(__fsub_rn(tau2, __fmul_rn(B2sq, __fmul_rn(dR, dR))), 0.f)), invA2);
+    const float hL = __fmul_rn(__fsqrt_rn(fmaxf(__fsub_rn(tau2, __fmul_rn(B2sq, __fmul_rn(dL, dL))), 0.f)), invA2);
+    const float xr = __fadd_rn(mx, __fadd_rn(__fmul_rn(r, dR), hR));
+    const float xl = __fadd_rn(mx, __fsub_rn(__fmul_rn(r, dL), hL));
+    const int px0 = f2i_clamped(ceilf(__fsub_rn(xl, 0.501f)), 0, vd.W);
+    const int px1 = f2i_clamped(floorf(__fsub_rn(xr, 0.499f)), -1, vd.W - 1);
+    if (px0 > px1) return false;
+    tx0 = px0 / kTile;
+    tx1 = px1 / kTile;
+    return true;
 }
 
 // One thread per list entry r; loops over the views of the batch so that the
@@ -79,7 +85,7 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Ba
         const ViewDesc &vd = b.v[v];
         const int64_t qidx = (int64_t)v * n_list + r;
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = make_float4(0.f, -INFINITY, 0.f, 0.f);
-        float4 r2 = make_float4(0.f, 0.f, sign, 0.f), e = make_float4(-1.f, 0.f, 0.f, 0.f);
+        float4 r2 = make_float4(0.f, 0.f, 0.f, sign), e = make_float4(-1.f, 0.f, 0.f, 0.f);
         SplatGeom g;
         if (o >= (1.f / 255.f) && splat_geometry(vd, mu, q, ls, g)) {
             const float z = g.tc[2], iz = 1.f / z;
@@ -111,10 +117,18 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Ba
                 const float xh = sqrtf(tau2 * fmaf(rr / B2, rr / B2, 1.f / (A2 * A2)));
                 const float dys = tau2 * rr / (B2 * B2 * xh);
                 r0 = make_float4(mx, my, rr, A2);
-                r1 = make_float4(B2, log2o, w, fmaxf(c0, 0.f));
-                r2 = make_float4(fmaxf(c1, 0.f), fmaxf(c2, 0.f), sign, 0.f);
+                r1 = make_float4(B2, log2o, w, yh);
+                r2 = make_float4(fmaxf(c0, 0.f), fmaxf(c1, 0.f), fmaxf(c2, 0.f), sign);
                 e = make_float4(tau2, yh, xh, dys);
-                for_each_tile(vd, mx, my, rr, A2, B2, e, [&](int t) { atomicAdd(tile_count + t, 1); });
+                int ty0, ty1;
+                if (tile_rows(vd, my, e, ty0, ty1)) {
+                    for (int ty = ty0; ty <= ty1; ++ty) {
+                        int tx0, tx1;
+                        if (!row_tiles(vd, mx, my, rr, A2, B2, e, ty, tx0, tx1)) continue;
+                        int *row = tile_count + vd.tile_base + ty * vd.tiles_x;
+                        for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(row + tx, 1);
+                    }
+                }
             }
         }
         rec[3 * qidx + 0] = r0;
@@ -184,21 +198,33 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(const int *__restrict_
     }
 }
 
+// One warp per list entry: the warp walks the entry's tile rows and its
+// lanes take the columns of a row in parallel, so the position-returning
+// atomics of a splat overlap instead of running one after another.
 __global__ void __launch_bounds__(256) scatter_kernel(const __grid_constant__ Batch b, const float4 *__restrict__ rec,
                                                       const float4 *__restrict__ ext, int *__restrict__ cursor,
                                                       uint32_t *__restrict__ pairs, int64_t cap) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (r >= b.n_list) return;
     for (int v = 0; v < b.n_views; ++v) {
+        const ViewDesc &vd = b.v[v];
         const int64_t qidx = (int64_t)v * b.n_list + r;
         const float4 e = ext[qidx];
+        int ty0, ty1;
         if (!(e.x > 0.f)) continue;
         const float4 r0 = rec[3 * qidx + 0];
+        if (!tile_rows(vd, r0.y, e, ty0, ty1)) continue;
         const float B2 = rec[3 * qidx + 1].x;
-        for_each_tile(b.v[v], r0.x, r0.y, r0.z, r0.w, B2, e, [&](int t) {
-            const int pos = atomicAdd(cursor + t, 1);
-            if ((int64_t)pos < cap) pairs[pos] = (uint32_t)qidx;
-        });
+        for (int ty = ty0; ty <= ty1; ++ty) {
+            int tx0, tx1;
+            if (!row_tiles(vd, r0.x, r0.y, r0.z, r0.w, B2, e, ty, tx0, tx1)) continue;
+            int *row = cursor + vd.tile_base + ty * vd.tiles_x;
+            for (int tx = tx0 + lane; tx <= tx1; tx += 32) {
+                const int pos = atomicAdd(row + tx, 1);
+                if ((int64_t)pos < cap) pairs[pos] = (uint32_t)qidx;
+            }
+        }
     }
 }
 
@@ -223,7 +249,7 @@ int launch_scan_tiles(const int *count, int total, int *offsets, int *cursor, in
 int launch_scatter(const Batch &b, const float4 *rec, const float4 *ext, int *cursor, uint32_t *pairs, int64_t cap,
                    cudaStream_t st) {
     if (b.n_list == 0) return 0;
-    scatter_kernel<<<(b.n_list + 255) / 256, 256, 0, st>>>(b, rec, ext, cursor, pairs, cap);
+    scatter_kernel<<<(int)(((int64_t)b.n_list * 32 + 255) / 256), 256, 0, st>>>(b, rec, ext, cursor, pairs, cap);
     return 0;
 }
 

@@ -159,14 +159,32 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(const __grid_constant_
             g_q[3] += (gqd - qd * qdot) * iq;
         }
         const int64_t row = out.rows_by_splat ? (int64_t)i : (int64_t)r;
+        float4 *oq = reinterpret_cast<float4 *>(out.quats) + row;
+        float4 *oh = reinterpret_cast<float4 *>(out.sh_color + 48 * row);
+        float4 *ow = reinterpret_cast<float4 *>(out.sh_weight + 16 * row);
+        if (out.accumulate) {  // add to the caller's running sums (several backward calls)
+            for (int k = 0; k < 3; ++k) g_mu[k] += out.means[3 * row + k];
+            const float4 pq = *oq;
+            g_q[0] += pq.x; g_q[1] += pq.y; g_q[2] += pq.z; g_q[3] += pq.w;
+            for (int k = 0; k < 3; ++k) g_ls[k] += out.log_scales[3 * row + k];
+            g_ol += out.opacity_logits[row];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                const float4 h = oh[k];
+                g_h[4 * k] += h.x; g_h[4 * k + 1] += h.y; g_h[4 * k + 2] += h.z; g_h[4 * k + 3] += h.w;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float4 h = ow[k];
+                g_hw[4 * k] += h.x; g_hw[4 * k + 1] += h.y; g_hw[4 * k + 2] += h.z; g_hw[4 * k + 3] += h.w;
+            }
+        }
         for (int k = 0; k < 3; ++k) out.means[3 * row + k] = g_mu[k];
-        reinterpret_cast<float4 *>(out.quats)[row] = make_float4(g_q[0], g_q[1], g_q[2], g_q[3]);
+        *oq = make_float4(g_q[0], g_q[1], g_q[2], g_q[3]);
         for (int k = 0; k < 3; ++k) out.log_scales[3 * row + k] = g_ls[k];
         out.opacity_logits[row] = g_ol;
-        float4 *oh = reinterpret_cast<float4 *>(out.sh_color + 48 * row);
 #pragma unroll
         for (int k = 0; k < 12; ++k) oh[k] = make_float4(g_h[4 * k], g_h[4 * k + 1], g_h[4 * k + 2], g_h[4 * k + 3]);
-        float4 *ow = reinterpret_cast<float4 *>(out.sh_weight + 16 * row);
 #pragma unroll
         for (int k = 0; k < 4; ++k) ow[k] = make_float4(g_hw[4 * k], g_hw[4 * k + 1], g_hw[4 * k + 2], g_hw[4 * k + 3]);
     }

@@ -12,19 +12,29 @@
 // gF = g.F.  Eq. 10 contracted with g gives, per pair,
 //   dL/da = A/(1 - a) + B w (g.c - gF),  dL/dw = B a (g.c - gF),
 //   dL/dc = B a w g,
-// and, unless a is clamped at 0.99, with a = 2^(log2 o - s),
-// s = (A2 u)^2 + (B2 dy)^2, u = dx - r dy:  dL/d(ln o) = a dL/da and
-// dL/ds = -ln2 a dL/da, chained to (mu'x, mu'y, r, A2, B2).
+// and, unless a is clamped at 0.99, dL/d(ln o) = a dL/da and
+// dL/ds = -ln2 a dL/da, chained to (mu'x, mu'y, r, A2, B2) below.  Each warp
+// walks only the tile rows that some lane's ellipse reaches.
 #include "common.cuh"
 #include "launch.h"
+#include "pair_eval.cuh"
 
 namespace soit {
 
+// Per contributing pair, with a = min(ar, 0.99), ar = 2^(log2 o - s),
+// s = e1^2 + e2^2, e1 = A2 u, e2 = B2 dy (u = dx - r dy):
+//   da = dL/da * a (0 if clamped) = dL/d(ln o) of the pair, and
+//   dL/ds = -ln2 da.  Summing K = -2 ln2 times
+//     Se = sum da e1, Sey = sum da e1 dy, See = sum da e1^2,
+//     Sdy = sum da dy, Sdyy = sum da dy^2
+// (the dy sums taken per tile row, where dy is constant) gives
+//   dL/dmu'x = -K A2 Se,  dL/dmu'y = K (A2 r Se - B2^2 Sdy),
+//   dL/dr = -K A2 Sey,    dL/dA2 = K See / A2,  dL/dB2 = K B2 Sdyy.
 __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(const __grid_constant__ Batch b,
                                                               const float4 *__restrict__ rec,
                                                               const int *__restrict__ offsets,
-                                                              const uint32_t *__restrict__ pairs, int64_t cap, uint32_t nrec,
-                                                              float4 *__restrict__ sgrad) {
+                                                              const uint32_t *__restrict__ pairs, int64_t cap,
+                                                              uint32_t nrec, float4 *__restrict__ sgrad) {
     __shared__ float4 sa[kTilePix];  // g0, g1, g2, A
     __shared__ float2 sb[kTilePix];  // B, gF
 
@@ -56,67 +66,73 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(const __grid_const
 
     for (int cb = start + warp * 32; cb < end; cb += kTilePix) {
         const int idx = cb + lane;
-        uint32_t q = idx < end ? pairs[idx] : 0xffffffffu;
+        const uint32_t q = idx < end ? pairs[idx] : 0xffffffffu;
         const bool valid = q < nrec;
-        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = make_float4(0.f, -INFINITY, 0.f, 0.f), a2 = a0;
+        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = make_float4(0.f, -INFINITY, 0.f, -1.f), a2 = a0;
         if (valid) {
             a0 = rec[3 * (int64_t)q + 0];
             a1 = rec[3 * (int64_t)q + 1];
             a2 = rec[3 * (int64_t)q + 2];
         }
-        const float rr = a0.z, A2 = a0.w, B2 = a1.x, log2o = a1.y, w = a1.z;
-        const float c0 = a1.w, c1 = a2.x, c2 = a2.y;
-        float S1 = 0.f, S2 = 0.f, S3 = 0.f, S4 = 0.f, S5 = 0.f, gl = 0.f, gw = 0.f;
+        const float rr = a0.z, A2 = a0.w, B2 = a1.x, log2o = a1.y, w = a1.z, yh = a1.w;
+        const SplatConsts sc = splat_consts(ox, oy, a0.x, a0.y, rr, A2, log2o);
+        const float dy0 = sc.dy0;
+        const float c0 = a2.x, c1 = a2.y, c2 = a2.z;
+        // rows of the tile this lane's ellipse can reach; the warp walks their union
+        int rlo = kTile, rhi = -1;
+        if (valid && yh >= 0.f) {
+            rlo = f2i_clamped(ceilf(-yh - dy0), 0, kTile);
+            rhi = f2i_clamped(floorf(yh - dy0), -1, kTile - 1);
+        }
+        rlo = __reduce_min_sync(0xffffffffu, rlo);
+        rhi = __reduce_max_sync(0xffffffffu, rhi);
+
+        float Se = 0.f, Sey = 0.f, See = 0.f, Sd = 0.f, Sdy = 0.f, Sdyy = 0.f, gw = 0.f;
         float gc0 = 0.f, gc1 = 0.f, gc2 = 0.f;
-        const float dx0 = ox - a0.x, dy0 = oy - a0.y;
-        for (int ky = 0; ky < kTile; ++ky) {
-            const float dy = dy0 + (float)ky;
-            const float e2 = B2 * dy;
-            const float e2sq = e2 * e2;
-#pragma unroll 4
+        for (int ky = rlo; ky <= rhi; ++ky) {
+            const RowTerms rt = row_terms(sc.A2dx0, dy0, sc.rA2, B2, ky);
+            float Rd = 0.f, Re = 0.f;
+#pragma unroll
             for (int kx = 0; kx < kTile; ++kx) {
-                const float dx = dx0 + (float)kx;
-                const float u = fmaf(-rr, dy, dx);
-                const float e1 = A2 * u;
-                const float arg = log2o - fmaf(e1, e1, e2sq);
-                if (arg >= -kLog2_255) {
+                const float e1 = col_e1(A2, rt.e10, kx);
+                const float sq = quad_s(e1, rt.e2sq);
+                if (sq <= sc.thr) {
                     const int k = ky * kTile + kx;
                     const float4 p = sa[k];
                     const float2 pb = sb[k];
-                    const float ar = exp2f(arg);
+                    const float ar = fast_exp2(log2o - sq);
                     const float a = fminf(ar, kAlphaMax);
-                    const float gcd = fmaf(p.x, c0, fmaf(p.y, c1, p.z * c2)) - pb.y;  // g.c - gF
-                    const float Bg = pb.x * gcd;
-                    const float dLda = fmaf(p.w, 1.f / (1.f - a), w * Bg);
-                    gw = fmaf(a, Bg, gw);
-                    const float Baw = pb.x * a * w;
-                    gc0 = fmaf(Baw, p.x, gc0);
-                    gc1 = fmaf(Baw, p.y, gc1);
-                    gc2 = fmaf(Baw, p.z, gc2);
-                    const float da = ar <= kAlphaMax ? dLda * a : 0.f;
-                    gl += da;
-                    const float G2 = -2.f * kLn2 * da;  // 2 dL/ds
-                    const float t = G2 * e1;
-                    S1 += t;
-                    S2 = fmaf(t, dy, S2);
-                    S3 = fmaf(t, u, S3);
-                    const float h = G2 * e2;
-                    S4 += h;
-                    S5 = fmaf(h, dy, S5);
+                    const float gcd = fmaf(p.x, c0, fmaf(p.y, c1, fmaf(p.z, c2, -pb.y)));  // g.c - g.F
+                    const float Ba = pb.x * a;
+                    const float dLda = fmaf(p.w, fast_rcp(1.f - a), w * (pb.x * gcd));
+                    gw = fmaf(Ba, gcd, gw);
+                    gc0 = fmaf(Ba, p.x, gc0);  // times w in the epilogue
+                    gc1 = fmaf(Ba, p.y, gc1);
+                    gc2 = fmaf(Ba, p.z, gc2);
+                    const float da = dLda * (ar > kAlphaMax ? 0.f : a);
+                    Rd += da;
+                    const float qd = da * e1;
+                    Re += qd;
+                    See = fmaf(qd, e1, See);
                 }
             }
+            Sd += Rd;
+            Sdy = fmaf(Rd, rt.dy, Sdy);
+            Sdyy = fmaf(Rd, rt.dy * rt.dy, Sdyy);
+            Se += Re;
+            Sey = fmaf(Re, rt.dy, Sey);
         }
         if (valid) {
-            // s = (A2 u)^2 + (B2 dy)^2, u = (px - mx) - r (py - my), dy = py - my
-            const float g_mx = -A2 * S1;
-            const float g_my = A2 * rr * S1 - B2 * S4;
-            const float g_r = -A2 * S2;
-            const float g_A2 = S3;
-            const float g_B2 = S5;
+            const float K = -2.f * kLn2;
+            const float g_mx = -K * A2 * Se;
+            const float g_my = K * (A2 * rr * Se - B2 * B2 * Sdy);
+            const float g_r = -K * A2 * Sey;
+            const float g_A2 = K * See / A2;
+            const float g_B2 = K * B2 * Sdyy;
             float4 *out = sgrad + 3 * (int64_t)q;
             atomicAdd(out + 0, make_float4(g_mx, g_my, g_r, g_A2));
-            atomicAdd(out + 1, make_float4(g_B2, gl, gw, gc0));
-            atomicAdd(reinterpret_cast<float2 *>(out + 2), make_float2(gc1, gc2));
+            atomicAdd(out + 1, make_float4(g_B2, Sd, gw, w * gc0));
+            atomicAdd(reinterpret_cast<float2 *>(out + 2), make_float2(w * gc1, w * gc2));
         }
     }
 }

@@ -1,10 +1,13 @@
 // raster_fwd.cu -- tile rasteriser of the OIT sums (Alg. 2 BAN / BAU, Eq. 7).
 //
-// One thread block per 16x16 tile of the batch, one thread per pixel.  The
-// tile's records are staged through shared memory 256 at a time; every
-// thread accumulates, over the tile's splats, P += a w c, Q += a w and
-// T *= (1 - a) (per-batch partial sums for P and Q to hold the FP32
-// rounding of long sums).  The epilogue depends on the mode:
+// One block per 16x16 tile; each thread owns a 1xS strip of pixels of one
+// row (S = 1, 2 or 4, a launch parameter; the exponent of the next pixel of
+// the strip costs one FMA), each warp owns 2S rows and skips, warp-uniformly,
+// splats whose cutoff ellipse misses those rows.  The tile's records are staged through shared
+// memory 256 at a time, already shifted to tile-relative offsets.  Every
+// pixel accumulates over the tile's splats P += a w c, Q += a w and
+// T *= (1 - a), with per-batch partial sums for P and Q to hold the FP32
+// rounding of long sums.  The epilogue depends on the mode:
 //   kRasterFused: combine with the view's frozen sums (P_F, Q_F, log T_F),
 //     write C = T c0 + (1 - T) P/Q, the L1 loss and the backward pixel state
 //     (g, A = T g.(F - c0), B = (1 - T)/Q, g.F) with g = sign(C - I)/(3HW).
@@ -14,19 +17,25 @@
 //     s log(1 - a) to the frozen planes (the delayed pre-render update).
 #include "common.cuh"
 #include "launch.h"
+#include "pair_eval.cuh"
 
 namespace soit {
 
-template <int kMode>
-__global__ void __launch_bounds__(kTilePix) raster_fwd_kernel(const __grid_constant__ Batch b,
-                                                              const float4 *__restrict__ rec,
-                                                              const int *__restrict__ offsets,
-                                                              const uint32_t *__restrict__ pairs, int64_t cap, uint32_t nrec,
-                                                              float bg0, float bg1, float bg2, float *loss,
-                                                              unsigned long long *contrib) {
-    __shared__ float4 s0[kTilePix], s1[kTilePix], s2[kTilePix];
-    __shared__ float red[kTilePix / 32];
-    __shared__ unsigned red_n[kTilePix / 32];
+constexpr int kFwdBatch = 256;    // records staged per round
+
+template <int kMode, bool kCount, int kStrip>
+__global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip == 2 ? 4 : 8)) raster_fwd_kernel(const __grid_constant__ Batch b,
+                                                                 const float4 *__restrict__ rec,
+                                                                 const int *__restrict__ offsets,
+                                                                 const uint32_t *__restrict__ pairs, int64_t cap,
+                                                                 uint32_t nrec, float bg0, float bg1, float bg2,
+                                                                 float *loss, unsigned long long *contrib) {
+    constexpr int kFwdThreads = kTilePix / kStrip;
+    constexpr int kStripsPerRow = kTile / kStrip;
+    __shared__ float4 s0[kFwdBatch], s1[kFwdBatch], s2[kFwdBatch];
+    __shared__ float ssign[kMode == kRasterSums ? kFwdBatch : 1];
+    __shared__ float red[kFwdThreads / 32];
+    __shared__ unsigned red_n[kFwdThreads / 32];
 
     const int gt = blockIdx.x;
     const int v = find_view(b, gt);
@@ -34,88 +43,120 @@ __global__ void __launch_bounds__(kTilePix) raster_fwd_kernel(const __grid_const
     const int lt = gt - vd.tile_base;
     const int ty = lt / vd.tiles_x, tx = lt - ty * vd.tiles_x;
     const int tid = threadIdx.x;
-    const int x = tx * kTile + (tid & (kTile - 1)), y = ty * kTile + (tid >> 4);
-    const bool inside = x < vd.W && y < vd.H;
-    const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+    const int ky = tid / kStripsPerRow, sx = (tid % kStripsPerRow) * kStrip;
+    const int wrow = (tid >> 5) * (32 / kStripsPerRow);  // first tile row of this warp
+    const float ox = (float)(tx * kTile) + 0.5f, oy = (float)(ty * kTile) + 0.5f;
 
     const int start = offsets[gt];
     const int end = (int)min((int64_t)offsets[gt + 1], cap);
 
-    float P0 = 0.f, P1 = 0.f, P2 = 0.f, Q = 0.f, T = 1.f, LT = 0.f;
+    float P0[kStrip], P1[kStrip], P2[kStrip], Q[kStrip], T[kStrip];
+#pragma unroll
+    for (int j = 0; j < kStrip; ++j) {
+        P0[j] = P1[j] = P2[j] = Q[j] = 0.f;
+        T[j] = kMode == kRasterSums ? 0.f : 1.f;  // log T in sums mode
+    }
     unsigned n_contrib = 0;
-    for (int base = start; base < end; base += kTilePix) {
-        const int n = min(kTilePix, end - base);
+
+    for (int base = start; base < end; base += kFwdBatch) {
+        const int n = min(kFwdBatch, end - base);
         __syncthreads();
-        if (tid < n) {
-            const uint32_t q = pairs[base + tid];
-            if (q < nrec) {
-                s0[tid] = rec[3 * (int64_t)q + 0];
-                s1[tid] = rec[3 * (int64_t)q + 1];
-                s2[tid] = rec[3 * (int64_t)q + 2];
-            } else {  // never written by this call's scatter: contributes nothing
-                s0[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-                s1[tid] = make_float4(0.f, -INFINITY, 0.f, 0.f);
-                s2[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = tid; k < n; k += kFwdThreads) {
+            const uint32_t q = pairs[base + k];
+            // staged: s0 = (A2 dx0, dy0, r A2, A2), s1 = (B2, thr, log2 o, yh),
+            //         s2 = (w c_r, w c_g, w c_b, w) (times the sign in sums mode)
+            float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = make_float4(0.f, -INFINITY, 0.f, -1.f);
+            float4 t2 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q < nrec) {  // never written by this call's scatter otherwise: contributes nothing
+                const float4 a0 = rec[3 * (int64_t)q + 0];
+                const float4 a1 = rec[3 * (int64_t)q + 1];
+                const float4 a2 = rec[3 * (int64_t)q + 2];
+                const SplatConsts c = splat_consts(ox, oy, a0.x, a0.y, a0.z, a0.w, a1.y);
+                t0 = make_float4(c.A2dx0, c.dy0, c.rA2, a0.w);
+                t1 = make_float4(a1.x, c.thr, a1.y, a1.w);
+                const float ws = kMode == kRasterSums ? a1.z * a2.w : a1.z;
+                t2 = make_float4(ws * a2.x, ws * a2.y, ws * a2.z, ws);
             }
+            s0[k] = t0;
+            s1[k] = t1;
+            s2[k] = t2;
+            if (kMode == kRasterSums) ssign[k] = q < nrec ? rec[3 * (int64_t)q + 2].w : 0.f;
         }
         __syncthreads();
-        float b0 = 0.f, b1 = 0.f, b2 = 0.f, bq = 0.f, bl = 0.f;
+        float b0[kStrip], b1[kStrip], b2[kStrip], bq[kStrip];
+#pragma unroll
+        for (int j = 0; j < kStrip; ++j) b0[j] = b1[j] = b2[j] = bq[j] = 0.f;
         for (int j = 0; j < n; ++j) {
             const float4 a0 = s0[j], a1 = s1[j];
-            const float dx = px - a0.x, dy = py - a0.y;
-            const float u = fmaf(-a0.z, dy, dx);
-            const float e1 = a0.w * u, e2 = a1.x * dy;
-            const float arg = a1.y - fmaf(e1, e1, e2 * e2);
-            if (arg >= -kLog2_255) {
-                const float a = fminf(exp2f(arg), kAlphaMax);
-                const float4 a2 = s2[j];
-                float aw = a * a1.z;
-                if (kMode == kRasterSums) aw *= a2.z;
-                b0 = fmaf(aw, a1.w, b0);
-                b1 = fmaf(aw, a2.x, b1);
-                b2 = fmaf(aw, a2.y, b2);
-                bq += aw;
-                if (kMode == kRasterSums)
-                    bl = fmaf(a2.z, log1pf(-a), bl);
-                else
-                    T = fmaf(-T, a, T);
-                ++n_contrib;
+            // warp-uniform: the ellipse misses this warp's rows
+            const float dlo = a0.y + (float)wrow;
+            if (dlo > a1.w || dlo + (float)(32 / kStripsPerRow - 1) < -a1.w) continue;
+            const RowTerms rt = row_terms(a0.x, a0.y, a0.z, a1.x, ky);
+            if (rt.e2sq > a1.y) continue;  // whole row outside (s >= e2^2 for every pixel of it)
+            const float4 a2 = s2[j];
+#pragma unroll
+            for (int p = 0; p < kStrip; ++p) {
+                const float sq = quad_s(col_e1(a0.w, rt.e10, sx + p), rt.e2sq);
+                if (sq <= a1.y) {
+                    const float a = fminf(fast_exp2(a1.z - sq), kAlphaMax);
+                    b0[p] = fmaf(a, a2.x, b0[p]);
+                    b1[p] = fmaf(a, a2.y, b1[p]);
+                    b2[p] = fmaf(a, a2.z, b2[p]);
+                    bq[p] = fmaf(a, a2.w, bq[p]);
+                    if (kMode == kRasterSums)
+                        T[p] = fmaf(ssign[j], log1pf(-a), T[p]);
+                    else
+                        T[p] = fmaf(-T[p], a, T[p]);
+                    if (kCount) n_contrib += (tx * kTile + sx + p < vd.W && ty * kTile + ky < vd.H) ? 1u : 0u;
+                }
             }
         }
-        P0 += b0; P1 += b1; P2 += b2; Q += bq; LT += bl;
+#pragma unroll
+        for (int p = 0; p < kStrip; ++p) {
+            P0[p] += b0[p];
+            P1[p] += b1[p];
+            P2[p] += b2[p];
+            Q[p] += bq[p];
+        }
     }
 
     const int64_t HW = (int64_t)vd.W * vd.H;
-    const int64_t pix = (int64_t)y * vd.W + x;
+    const int y = ty * kTile + ky;
     float my_loss = 0.f;
-    if (inside) {
+    const float inv3hw = 1.f / (3.f * (float)HW);
+#pragma unroll
+    for (int p = 0; p < kStrip; ++p) {
+        const int x = tx * kTile + sx + p;
+        if (x >= vd.W || y >= vd.H) continue;
+        const int64_t pix = (int64_t)y * vd.W + x;
         if (kMode == kRasterSums) {
             float *fz = vd.frozen;
-            fz[pix] += P0;
-            fz[HW + pix] += P1;
-            fz[2 * HW + pix] += P2;
-            fz[3 * HW + pix] += Q;
-            fz[4 * HW + pix] += LT;
+            fz[pix] += P0[p];
+            fz[HW + pix] += P1[p];
+            fz[2 * HW + pix] += P2[p];
+            fz[3 * HW + pix] += Q[p];
+            fz[4 * HW + pix] += T[p];
         } else {
             const float *fz = vd.frozen;
-            const float Pt0 = P0 + fz[pix], Pt1 = P1 + fz[HW + pix], Pt2 = P2 + fz[2 * HW + pix];
-            const float Qt = Q + fz[3 * HW + pix];
-            const float Tt = T * expf(fz[4 * HW + pix]);
+            const float Pt0 = P0[p] + fz[pix], Pt1 = P1[p] + fz[HW + pix], Pt2 = P2[p] + fz[2 * HW + pix];
+            const float Qt = Q[p] + fz[3 * HW + pix];
+            const float Tt = T[p] * expf(fz[4 * HW + pix]);
             const float invQ = Qt > 0.f ? 1.f / Qt : 0.f;
             const float F0 = Pt0 * invQ, F1 = Pt1 * invQ, F2 = Pt2 * invQ;
             const float omT = 1.f - Tt;
             const float C0 = fmaf(Tt, bg0, omT * F0), C1 = fmaf(Tt, bg1, omT * F1), C2 = fmaf(Tt, bg2, omT * F2);
             float *img = vd.image + 3 * pix;
-            img[0] = C0; img[1] = C1; img[2] = C2;
+            img[0] = C0;
+            img[1] = C1;
+            img[2] = C2;
             float *st = vd.state;
             if (kMode == kRasterFused) {
                 const float *tg = vd.target + 3 * pix;
                 const float d0 = C0 - tg[0], d1 = C1 - tg[1], d2 = C2 - tg[2];
-                my_loss = fabsf(d0) + fabsf(d1) + fabsf(d2);
-                const float inv = 1.f / (3.f * (float)HW);
-                const float g0 = d0 > 0.f ? inv : (d0 < 0.f ? -inv : 0.f);
-                const float g1 = d1 > 0.f ? inv : (d1 < 0.f ? -inv : 0.f);
-                const float g2 = d2 > 0.f ? inv : (d2 < 0.f ? -inv : 0.f);
+                my_loss += fabsf(d0) + fabsf(d1) + fabsf(d2);
+                const float g0 = d0 > 0.f ? inv3hw : (d0 < 0.f ? -inv3hw : 0.f);
+                const float g1 = d1 > 0.f ? inv3hw : (d1 < 0.f ? -inv3hw : 0.f);
+                const float g2 = d2 > 0.f ? inv3hw : (d2 < 0.f ? -inv3hw : 0.f);
                 st[pix] = g0;
                 st[HW + pix] = g1;
                 st[2 * HW + pix] = g2;
@@ -130,10 +171,8 @@ __global__ void __launch_bounds__(kTilePix) raster_fwd_kernel(const __grid_const
                 st[4 * HW + pix] = Qt;
             }
         }
-    } else {
-        n_contrib = 0;
     }
-    if ((kMode == kRasterFused && loss) || contrib) {
+    if ((kMode == kRasterFused && loss) || kCount) {
         float l = my_loss;
         unsigned c = n_contrib;
 #pragma unroll
@@ -141,35 +180,64 @@ __global__ void __launch_bounds__(kTilePix) raster_fwd_kernel(const __grid_const
             l += __shfl_xor_sync(0xffffffffu, l, off);
             c += __shfl_xor_sync(0xffffffffu, c, off);
         }
-        if ((tid & 31) == 0) { red[tid >> 5] = l; red_n[tid >> 5] = c; }
+        if ((tid & 31) == 0) {
+            red[tid >> 5] = l;
+            red_n[tid >> 5] = c;
+        }
         __syncthreads();
         if (tid == 0) {
             float ls = 0.f;
             unsigned long long cs = 0;
-            for (int k = 0; k < kTilePix / 32; ++k) { ls += red[k]; cs += red_n[k]; }
-            if (kMode == kRasterFused && loss && ls != 0.f) atomicAdd(loss, ls / (3.f * (float)HW));
-            if (contrib && cs) atomicAdd(contrib, cs);
+            for (int k = 0; k < kFwdThreads / 32; ++k) {
+                ls += red[k];
+                cs += red_n[k];
+            }
+            if (kMode == kRasterFused && loss && ls != 0.f) atomicAdd(loss, ls * inv3hw);
+            if (kCount && contrib && cs) atomicAdd(contrib, cs);
         }
     }
 }
 
-int launch_raster_fwd(const Batch &b, int mode, const float4 *rec, const int *offsets, const uint32_t *pairs,
-                      int64_t cap, const float bg[3], float *loss, unsigned long long *contrib, cudaStream_t st) {
-    const uint32_t nrec = (uint32_t)((int64_t)b.n_views * b.n_list);
+template <int kMode, int kStrip>
+static void launch_strip(const Batch &b, bool count, const float4 *rec, const int *offsets, const uint32_t *pairs,
+                         int64_t cap, uint32_t nrec, const float bg[3], float *loss, unsigned long long *contrib,
+                         cudaStream_t st) {
+    const dim3 grid(b.total_tiles), block(kTilePix / kStrip);
+    if (count)
+        raster_fwd_kernel<kMode, true, kStrip><<<grid, block, 0, st>>>(b, rec, offsets, pairs, cap, nrec, bg[0], bg[1],
+                                                                        bg[2], loss, contrib);
+    else
+        raster_fwd_kernel<kMode, false, kStrip><<<grid, block, 0, st>>>(b, rec, offsets, pairs, cap, nrec, bg[0],
+                                                                         bg[1], bg[2], loss, contrib);
+}
+
+template <int kMode>
+static void launch_mode(const Batch &b, int strip, bool count, const float4 *rec, const int *offsets,
+                        const uint32_t *pairs, int64_t cap, uint32_t nrec, const float bg[3], float *loss,
+                        unsigned long long *contrib, cudaStream_t st) {
+    if (strip == 4)
+        launch_strip<kMode, 4>(b, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, st);
+    else if (strip == 2)
+        launch_strip<kMode, 2>(b, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, st);
+    else
+        launch_strip<kMode, 1>(b, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, st);
+}
+
+int launch_raster_fwd(const Batch &b, int mode, int strip, const float4 *rec, const int *offsets,
+                      const uint32_t *pairs, int64_t cap, const float bg[3], float *loss, unsigned long long *contrib,
+                      cudaStream_t st) {
     if (b.total_tiles == 0) return 0;
-    const dim3 grid(b.total_tiles);
+    const uint32_t nrec = (uint32_t)((int64_t)b.n_views * b.n_list);
+    const bool count = contrib != nullptr;
     switch (mode) {
         case kRasterFused:
-            raster_fwd_kernel<kRasterFused><<<grid, kTilePix, 0, st>>>(b, rec, offsets, pairs, cap, nrec, bg[0], bg[1],
-                                                                      bg[2], loss, contrib);
+            launch_mode<kRasterFused>(b, strip, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, st);
             break;
         case kRasterAux:
-            raster_fwd_kernel<kRasterAux><<<grid, kTilePix, 0, st>>>(b, rec, offsets, pairs, cap, nrec, bg[0], bg[1], bg[2],
-                                                                    loss, contrib);
+            launch_mode<kRasterAux>(b, strip, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, st);
             break;
         default:
-            raster_fwd_kernel<kRasterSums><<<grid, kTilePix, 0, st>>>(b, rec, offsets, pairs, cap, nrec, bg[0], bg[1],
-                                                                     bg[2], loss, contrib);
+            launch_mode<kRasterSums>(b, strip, false, rec, offsets, pairs, cap, nrec, bg, nullptr, nullptr, st);
             break;
     }
     return 0;

@@ -111,7 +111,8 @@ def _stream_ptr(stream: Optional[torch.cuda.Stream] = None) -> int:
 class Renderer:
     """A SparseOIT context: active set, per-view frozen sums, batched fwd / bwd."""
 
-    def __init__(self, n_splats: int, view_sizes: Sequence[Sequence[int]], max_pairs: int = 0):
+    def __init__(self, n_splats: int, view_sizes: Sequence[Sequence[int]], max_pairs: int = 0,
+                 fwd_pixels_per_thread: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("sparseoit needs a CUDA device")
         self.lib = _lib.load()
@@ -122,6 +123,7 @@ class Renderer:
         hs = (ctypes.c_int32 * nv)(*[h for _, h in self.view_sizes])
         cfg = _lib.Config()
         cfg.max_pairs = int(max_pairs)
+        cfg.fwd_pixels_per_thread = int(fwd_pixels_per_thread)
         self._ctx = ctypes.c_void_p()
         rc = self.lib.sparseoit_create(ctypes.byref(self._ctx), self.n, nv, ws, hs, ctypes.byref(cfg))
         if rc != _lib.OK:
@@ -219,11 +221,12 @@ class Renderer:
         return images, loss
 
     def backward(self, splats: SplatParams, grad_images: Optional[Sequence[torch.Tensor]] = None,
-                 rows_by_splat: bool = False, stream=None, out: Optional[Dict[str, torch.Tensor]] = None):
+                 rows_by_splat: bool = False, stream=None, out: Optional[Dict[str, torch.Tensor]] = None,
+                 accumulate: bool = False):
         """Gradients of the last forward's loss for the active splats (App. B).
 
         rows_by_splat=False: compact [n_active, ...] rows in active-index order;
-        True: full [N, ...] arrays, inactive rows zero."""
+        True: full [N, ...] arrays, inactive rows zero.  accumulate=True adds to `out`."""
         s = splats_struct(splats)
         rows = self.n if rows_by_splat else self.n_active
         if out is None:
@@ -235,6 +238,7 @@ class Renderer:
         for name in PARAM_NAMES + ("sigma",):
             setattr(g, name, out[name].data_ptr())
         g.rows_by_splat = 1 if rows_by_splat else 0
+        g.accumulate = 1 if accumulate else 0
         gptr = None
         if grad_images is not None:
             gi = [x.contiguous().float() for x in grad_images]

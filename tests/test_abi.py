@@ -61,8 +61,8 @@ int main(void) {
   F(sparseoit_camera, fx) F(sparseoit_camera, width) F(sparseoit_camera, height)
   F(sparseoit_splats, sh_color) F(sparseoit_splats, sh_dtype) F(sparseoit_splats, sigma) F(sparseoit_splats, bg)
   F(sparseoit_splats, n)
-  F(sparseoit_grads, sigma) F(sparseoit_grads, rows_by_splat)
-  F(sparseoit_config, max_pairs) F(sparseoit_config, reserved)
+  F(sparseoit_grads, sigma) F(sparseoit_grads, rows_by_splat) F(sparseoit_grads, accumulate)
+  F(sparseoit_config, max_pairs) F(sparseoit_config, fwd_pixels_per_thread) F(sparseoit_config, reserved)
   F(sparseoit_kernel_time, launches) F(sparseoit_kernel_time, total_ms)
   return 0;
 }
