@@ -45,13 +45,14 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# FP32 operations of one contributing (splat, pixel) pair, counted from the
-# arithmetic of the kernels' algorithm ("Roofline"): forward
-# 16 (offset 2, quadratic form 5, threshold 1, exp 1, clamp 1, weight 1,
-# P/Q 4, T 1), backward 44 (forward part 10, Eq. 10 terms 16, chain to the
-# screen parameters 10, accumulation 8).
-FLOPS_FWD_PER_EVAL = 16
-FLOPS_BWD_PER_EVAL = 44
+# FP32 flops (an FMA counts 2, exp2 / reciprocal / min 1 each) of one
+# contributing (splat, pixel) pair in the algorithm the kernels run: forward
+# 22 = offsets 2, u 2, e1 1, e2 1, s 3, log2 alpha 1, exp2 1, clamp 1,
+# P 6, Q 2, T 2; backward 39 = the same 12 up to the clamp, g.c - g.F 6,
+# B (g.c - g.F) 1, 1 - a 1, reciprocal 1, dL/da 3, B a 1, dL/dw 2,
+# dL/dc 6, da 1, chain sums 6.
+FLOPS_FWD_PER_EVAL = 22
+FLOPS_BWD_PER_EVAL = 39
 
 
 def fp32_peak_tflops(sm_mhz: float) -> float:
@@ -107,6 +108,23 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def rank_camera_seeds(rank: int, base_seed: int):
+    """Weak scaling over views: rank k renders its own view of the same scene
+    (camera seed base + 3 + 17 k, target seed base + 1 + 17 k)."""
+    return base_seed + 3 + 17 * rank, base_seed + 1 + 17 * rank
+
+
+def reduce_over_ranks(ms: float, evals: float, device="cpu"):
+    """Whole-job figures over the ranks: the max step time and the summed evals."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([float(evals)], dtype=torch.float64, device=device)
+    dist.all_reduce(e)
+    return float(t.item()), float(e.item())
 
 
 def _dist():
@@ -199,12 +217,243 @@ def run_reference(args):
 
 
 def cpu_baseline_sample(scene, cam, target, mask, budget_s=15.0):
-    """The oracle as it stands, timed on the host cores: one fwd+bwd on a window sized to ~budget_s."""
+    """The oracle as it stands, timed on the host cores: fwd+bwd on a window sized to ~budget_s
+    (repeated when even the whole view takes less)."""
     import oracle
     win = _calibrated_window(scene, cam, target, mask, budget_s)
     dt, evals = _oracle_timing(scene, cam, target, mask, win, 1, 0)
+    reps = 1
+    if dt < 0.5 * budget_s:
+        reps = int(min(20, max(1, budget_s // max(dt, 1e-3))))
+        dt, evals = _oracle_timing(scene, cam, target, mask, win, reps, 0)
     return {"value": evals / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": _sample_text(win, evals, dt, 1)}
+            "sample": _sample_text(win, evals, dt, reps)}
+
+
+def _graph_time(torch, stream, flush, fn, steps, warmup):
+    """Capture fn() once as a CUDA graph; mean CUDA-event time of `steps` replays (L2 flushed between)."""
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            fn()
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            fn()
+        g.replay()
+        stream.synchronize()
+        times = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+            stream.synchronize()
+            times.append(a.elapsed_time(b))
+    del g
+    return float(np.mean(times))
+
+
+def _grad_out(torch, rows, dev):
+    out = {k: torch.zeros((rows,) + s, dtype=torch.float32, device=dev) for k, s in
+           (("means", (3,)), ("quats", (4,)), ("log_scales", (3,)), ("opacity_logits", ()),
+            ("sh_color", (16, 3)), ("sh_weight", (16,)))}
+    out["sigma"] = torch.zeros(1, dtype=torch.float32, device=dev)
+    return out
+
+
+def run_batched(args):
+    """3M splats, 16 views of four sizes in one call (CUDA-graph replay), 5 % active:
+    autotuned forward strip vs one pixel per thread vs 16 separate calls."""
+    import torch
+    import __graft_entry__
+    from paper_2605_13855_gb300 import scenes
+    from paper_2605_13855_gb300.renderer import Renderer, SplatParams
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    c = scenes.BATCHED
+    n = c["n"]
+    scene = scenes.unbounded_scene(n, c["seed"])
+    cams = scenes.batched_cameras()
+    sizes = [(cm["width"], cm["height"]) for cm in cams]
+    views = list(range(len(cams)))
+    mask = torch.as_tensor(scenes.proxy_active_mask(scene["means"], c["active"], c["seed"] + 2), device=dev)
+    sp = SplatParams.from_numpy(scene, device=dev)
+    targets = [torch.as_tensor(scenes.uniform_target(c["seed"] + 1 + 17 * k, W, H), device=dev)
+               for k, (W, H) in enumerate(sizes)]
+    imgs = [torch.empty((H, W, 3), dtype=torch.float32, device=dev) for (W, H) in sizes]
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {}
+    with torch.cuda.stream(stream):
+        rA = Renderer(n, sizes, max_pairs=1 << 27)
+        rA.set_active(mask, stream=stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for v, cm in enumerate(cams):
+            rA.commit_frozen(sp, cm, v, mode="recompute", stream=stream)
+        b.record(stream)
+        stream.synchronize()
+        res["commit_recompute_16_views_ms"] = a.elapsed_time(b)
+        out = _grad_out(torch, rA.n_active, dev)
+        rA.set_counting(True)
+        rA.forward(sp, cams, views, targets=targets, stream=stream, images=imgs, loss=loss)
+        rA.status(stream)
+        rA.set_counting(False)
+        M, E = rA.last_counts(stream)
+        tune = rA.autotune(sp, cams, views, targets=targets, stream=stream)
+
+        def batched_step(r=rA):
+            r.forward(sp, cams, views, targets=targets, stream=stream, images=imgs, loss=loss)
+            r.backward(sp, stream=stream, out=out)
+
+        res["autotuned_ms"] = _graph_time(torch, stream, flush, batched_step, args.steps, args.warmup)
+
+        def separate_step():
+            for k in views:
+                rA.forward(sp, [cams[k]], [k], targets=[targets[k]], stream=stream, images=[imgs[k]], loss=loss)
+                rA.backward(sp, stream=stream, out=out, accumulate=k > 0)
+
+        res["separate_calls_ms"] = _graph_time(torch, stream, flush, separate_step, args.steps, args.warmup)
+        rA.status(stream)
+        rA.close()
+        rB = Renderer(n, sizes, max_pairs=1 << 27, fwd_pixels_per_thread=1)
+        rB.set_active(mask, stream=stream)
+        for v, cm in enumerate(cams):
+            rB.commit_frozen(sp, cm, v, mode="recompute", stream=stream)
+        res["fixed_1px_ms"] = _graph_time(torch, stream, flush, lambda: batched_step(rB), args.steps, args.warmup)
+        rB.status(stream)
+        rB.close()
+    ms = res["autotuned_ms"]
+    line = {"metric": "ms per fwd+bwd iteration & splat-pixel evals/s, 3M splats, 16 views of uneven size, 5% active",
+            "value": E / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batched: 3M splats (unbounded scene), 16 views (4 x 640x480, 800x800, 1297x840, "
+                                   "1600x1064), 5% active, fused L1, one call + CUDA graph",
+                       "evals_per_step": E, "pairs_per_step": M, "n_active": int(mask.sum().item())},
+            "variants_ms": {"autotuned_one_call": ms, "fixed_1px_per_thread_one_call": res["fixed_1px_ms"],
+                            "16_separate_calls": res["separate_calls_ms"]},
+            "autotune": tune, "commit_recompute_16_views_ms": res["commit_recompute_16_views_ms"]}
+    print(json.dumps(line), flush=True)
+
+
+def _err_stats(gpu, ref):
+    d = np.abs(gpu - ref)
+    return {"max_rel": float(d.max() / max(np.abs(ref).max(), 1e-30)),
+            "mean_rel": float(d.mean() / max(np.abs(ref).mean(), 1e-30))}
+
+
+def run_precision(args):
+    """3M splats, 8 views 1297x840, 5 % active: BF16-stored SH vs FP32, time and error against
+    the FP64 oracle on the centred 256x256 crop of every view (dL/dC zero outside it)."""
+    import torch
+    import __graft_entry__
+    import oracle
+    from paper_2605_13855_gb300 import scenes
+    from paper_2605_13855_gb300.renderer import Renderer, SplatParams
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    c = scenes.PRECISION
+    n = c["n"]
+    scene = scenes.unbounded_scene(n, c["seed"])
+    cams = scenes.precision_cameras()
+    W, H = c["width"], c["height"]
+    views = list(range(len(cams)))
+    mask_np = scenes.proxy_active_mask(scene["means"], c["active"], c["seed"] + 2)
+    mask = torch.as_tensor(mask_np, device=dev)
+    x0, y0, x1, y1 = c["crop"]
+    rng = np.random.default_rng(c["seed"] + 9)
+    gs = []
+    for _ in views:
+        g = np.zeros((H, W, 3))
+        g[y0:y1, x0:x1] = rng.normal(size=(y1 - y0, x1 - x0, 3))
+        gs.append(g)
+    gts = [torch.as_tensor(g, dtype=torch.float32, device=dev) for g in gs]
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    imgs = [torch.empty((H, W, 3), dtype=torch.float32, device=dev) for _ in views]
+    results = {}
+    sc16 = dict(scene)
+    for k in ("sh_color", "sh_weight"):
+        sc16[k] = torch.as_tensor(scene[k]).to(torch.bfloat16).float().numpy()
+    act = mask_np.astype(bool)
+    rows = np.where(act)[0]
+    for label, dt in (("fp32", torch.float32), ("bf16", torch.bfloat16)):
+        sp = SplatParams.from_numpy(scene, device=dev, sh_dtype=dt)
+        with torch.cuda.stream(stream):
+            r = Renderer(n, [(W, H)] * len(views), max_pairs=1 << 27)
+            r.set_active(mask, stream=stream)
+            for v, cm in enumerate(cams):
+                r.commit_frozen(sp, cm, v, mode="recompute", stream=stream)
+            out = _grad_out(torch, r.n_active, dev)
+
+            def step():
+                r.forward(sp, cams, views, stream=stream, images=imgs)
+                r.backward(sp, gts, stream=stream, out=out)
+
+            ms = _graph_time(torch, stream, flush, step, args.steps, args.warmup)
+            step()
+            stream.synchronize()
+            r.status(stream)
+        img_np = [im.cpu().numpy().astype(np.float64) for im in imgs]
+        grads = {k: v.cpu().numpy().astype(np.float64) for k, v in out.items()}
+        r.close()
+        del sp
+        results[label] = {"ms": ms, "img": img_np, "grads": grads}
+    # FP64 oracle on the crops, with FP32 and with BF16-rounded coefficients
+    # Pairs within a relative 3e-4 of the 1/255 cut (or of the 0.99 clamp) may be decided
+    # differently in FP32 and FP64: each pixel / gradient element is allowed the oracle's bound
+    # on what those pairs can change ("flip"); the raw maximum is reported beside.  Splats at a
+    # max(0, .) kink or the near plane are excluded and counted.
+    errs = {}
+    for ref_label, ref_scene in (("oracle_fp32_inputs", scene), ("oracle_bf16_inputs", sc16)):
+        ref_imgs, flips, tot = [], [], None
+        for v, cm in enumerate(cams):
+            rr_ = oracle.render(ref_scene, cm, window=c["crop"], amb_band=3e-4)
+            ref_imgs.append(rr_["image"][y0:y1, x0:x1])
+            flips.append(rr_["flip"][y0:y1, x0:x1])
+            rg = oracle.backward_full(ref_scene, cm, rr_["sums"], gs[v], active=act, window=c["crop"],
+                                      amb_band=3e-4, want_flip=True)
+            if tot is None:
+                tot = {"grads": rg["grads"][rows], "flip": rg["flip"][rows], "amb": rg["amb"][rows]}
+            else:
+                tot["grads"] += rg["grads"][rows]
+                tot["flip"] += rg["flip"][rows]
+                tot["amb"] |= rg["amb"][rows]
+        groups = dict(means=(0, 3), quats=(3, 7), log_scales=(7, 10), opacity_logits=(10, 11),
+                      sh_color=(11, 59), sh_weight=(59, 75))
+        keep = (tot["amb"] & 2) == 0
+        ri, fl = np.stack(ref_imgs), np.stack(flips)
+        for label in ("fp32", "bf16"):
+            gi = np.stack([im[y0:y1, x0:x1] for im in results[label]["img"]])
+            d = np.abs(gi - ri).max(axis=3)
+            dm = np.maximum(d - fl, 0.0)
+            e = {"image": {"max_rel": float(dm.max() / np.abs(ri).max()),
+                           "mean_rel": float(d.mean() / np.abs(ri).mean()),
+                           "raw_max_rel": float(d.max() / np.abs(ri).max()),
+                           "pixels_with_allowance": float((fl > 0).mean())}}
+            for name, (lo, hi) in groups.items():
+                gg = results[label]["grads"][name].reshape(len(rows), -1)[keep]
+                rr = tot["grads"][keep, lo:hi]
+                dd = np.abs(gg - rr)
+                e[name] = {"max_rel": float(np.maximum(dd - tot["flip"][keep, lo:hi], 0.0).max() /
+                                            max(np.abs(rr).max(), 1e-30)),
+                           "mean_rel": float(dd.mean() / max(np.abs(rr).mean(), 1e-30)),
+                           "raw_max_rel": float(dd.max() / max(np.abs(rr).max(), 1e-30))}
+            e["kink_excluded_splats"] = float(1.0 - keep.mean())
+            errs[f"{label}_vs_{ref_label}"] = e
+    line = {"metric": "ms per fwd+bwd iteration, 3M splats, 8 views 1297x840, 5% active: BF16 vs FP32 SH storage",
+            "value": results["fp32"]["ms"] / results["bf16"]["ms"], "unit": "speedup of BF16 SH over FP32 SH",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": results["bf16"]["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 SH, f32 math",
+            "data": "synthetic",
+            "config": {"workload": "precision: 3M splats (unbounded scene), 8 views 1297x840, 5% active, linear "
+                                   "loss on the 256x256 crop [520,776)x[292,548) of each view",
+                       "ms_fp32_sh": results["fp32"]["ms"], "ms_bf16_sh": results["bf16"]["ms"]},
+            "errors": errs}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -220,11 +469,22 @@ def main():
                     help="comma list of active fractions to time (default 0.01,0.05,0.2,1); must include 0.05")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end and stage-update timings")
     ap.add_argument("--fwd-strip", type=int, default=0, help="forward raster pixels per thread (1, 2, 4; 0 = default)")
+    ap.add_argument("--proj-lanes", type=int, default=0, help="projection lanes per splat (4, 16; 0 = default)")
+    ap.add_argument("--bwd-group", type=int, default=0, help="backward grouping by centre cell (1 on, -1 off, 0 default)")
+    ap.add_argument("--workload", default="unbounded", choices=["unbounded", "batched", "precision"],
+                    help="unbounded (default line): 1M splats, one view; batched: 3M splats, 16 views; "
+                         "precision: 3M splats, 8 views, BF16 vs FP32 SH")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batched":
+        run_batched(args)
+        return
+    if args.workload == "precision":
+        run_precision(args)
         return
 
     import torch
@@ -249,8 +509,9 @@ def main():
     W, H = scenes.UNBOUNDED["width"], scenes.UNBOUNDED["height"]
     scene = scenes.unbounded_scene(n, scenes.UNBOUNDED["seed"])
     # weak scaling: every rank renders its own view of the same scene
-    cam = scenes.random_camera(scenes.UNBOUNDED["seed"] + 3 + 17 * rank, W, H)
-    target_np = scenes.uniform_target(scenes.UNBOUNDED["seed"] + 1 + 17 * rank, W, H)
+    cam_seed, target_seed = rank_camera_seeds(rank, scenes.UNBOUNDED["seed"])
+    cam = scenes.random_camera(cam_seed, W, H)
+    target_np = scenes.uniform_target(target_seed, W, H)
     sp = SplatParams.from_numpy(scene, device=dev)
     target = torch.as_tensor(target_np, device=dev)
     stream = torch.cuda.Stream(device=dev)
@@ -260,7 +521,8 @@ def main():
         m = scenes.proxy_active_mask(scene["means"], fraction, scenes.UNBOUNDED["seed"] + 2 + seed_shift)
         return torch.as_tensor(m, device=dev)
 
-    r = Renderer(n, [(W, H)], max_pairs=1 << 27, fwd_pixels_per_thread=args.fwd_strip)
+    r = Renderer(n, [(W, H)], max_pairs=1 << 27, fwd_pixels_per_thread=args.fwd_strip,
+                 proj_lanes_per_splat=args.proj_lanes, bwd_group_by_cell=args.bwd_group)
     img = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
     loss = torch.empty(1, dtype=torch.float32, device=dev)
 
@@ -337,7 +599,7 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
         for f in fr_list:
-            results[f] = timed(f, args.steps, args.warmup, profile=(f == HEADLINE_FRACTION))
+            results[f] = timed(f, args.steps, args.warmup, profile=(f in (HEADLINE_FRACTION, 1.0)))
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
@@ -346,13 +608,7 @@ def main():
     head = results[HEADLINE_FRACTION]
     ms = head["ms"]
     if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        e = torch.tensor([float(head["E"])], device=dev)
-        dist.all_reduce(e)
-        total_E = float(e.item())
+        ms, total_E = reduce_over_ranks(ms, head["E"], device=dev)
     else:
         total_E = float(head["E"])
     value = total_E / (ms * 1e-3)
@@ -414,10 +670,7 @@ def main():
                 e_times.append(a.elapsed_time(b))
         e2e_ms = float(np.mean(e_times))
         if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+            e2e_ms, _ = reduce_over_ranks(e2e_ms, 0.0, device=dev)
 
     if rank != 0:
         if ws > 1:
@@ -463,6 +716,8 @@ def main():
         "fractions": {str(f): {"ms": v["ms"], "ms_min": v["ms_min"], "evals": v["E"], "pairs": v["M"],
                                "n_active": v["n_active"], "commit_recompute_ms": v["commit_recompute_ms"]}
                       for f, v in results.items()},
+        "per_kernel_ms_full": None if full is None or not full["prof"] else {
+            k: {"launches": n_, "avg_ms": t_ / max(1, n_)} for k, (n_, t_) in full["prof"].items()},
         "stage_update": {"set_active_ms": set_active_ms, "commit_incremental_ms": commit_inc_ms},
         "per_kernel_ms": per_kernel,
         "roofline": roofline,

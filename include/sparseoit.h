@@ -130,7 +130,13 @@ typedef struct {
     int32_t fwd_pixels_per_thread; /* forward raster: pixels per thread, 1, 2 or 4
                                       (256 / 128 / 64 threads per 16x16 tile);
                                       0 = default (4)                          */
-    int32_t reserved[5];
+    int32_t proj_lanes_per_splat;  /* projection: lanes per splat, 4 or 16;
+                                      0 = default (4)                          */
+    int32_t bwd_group_by_cell;     /* backward raster: order each round of a
+                                      tile's splats by the 4x4-pixel cell of
+                                      their centre before assigning warps;
+                                      1 = on, -1 = off, 0 = default (off)      */
+    int32_t reserved[3];
 } sparseoit_config;
 
 /* Create a context for a scene of max_splats splats and n_views training
@@ -190,6 +196,25 @@ int sparseoit_forward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const 
  * same parameter values as in the forward. */
 int sparseoit_backward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const float *const *d_grad_images,
                        sparseoit_grads *out, void *stream);
+
+/* Result of sparseoit_autotune. */
+typedef struct {
+    int32_t fwd_pixels_per_thread;   /* chosen candidate (1, 2 or 4)          */
+    int32_t n_candidates;
+    int32_t candidates[4];           /* the candidates tried                  */
+    float ms[4];                     /* mean forward time of each candidate   */
+} sparseoit_tuning;
+
+/* Autotuner: times the forward raster's per-thread pixel strip (1x1, 1x2 and
+ * 1x4 pixels of the 16x16 tile, i.e. 256 / 128 / 64 threads per tile) on
+ * this exact batch -- the arguments are those of sparseoit_forward, which it
+ * runs (1 warm-up + `reps` timed calls per candidate, CUDA events on
+ * `stream`) -- and keeps the fastest for later calls.  The outputs of the
+ * last call are valid forward outputs.  Synchronises `stream`; not for use
+ * during stream capture. */
+int sparseoit_autotune(sparseoit_ctx *ctx, const sparseoit_splats *splats, const sparseoit_camera *cams,
+                       const int32_t *views, int32_t n_views, float *const *d_images, const float *const *d_targets,
+                       float *d_loss, int32_t reps, sparseoit_tuning *out, void *stream);
 
 /* Enlarge the pair arena to at least max_pairs entries (synchronises). */
 int sparseoit_reserve_pairs(sparseoit_ctx *ctx, int64_t max_pairs);

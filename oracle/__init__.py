@@ -8,6 +8,7 @@ from .core import (  # noqa: F401
     NPARAM,
     build,
     backward,
+    backward_full,
     compose,
     num_threads,
     project,

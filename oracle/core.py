@@ -61,12 +61,12 @@ def _load():
             lib.oracle_project.argtypes = params + [_dp, ctypes.c_int, ctypes.c_int, _dp]
             lib.oracle_project.restype = ctypes.c_int
             lib.oracle_render_sums.argtypes = params + [
-                _dp, ctypes.c_int, ctypes.c_int, _u8p, ctypes.c_int, _ip, ctypes.c_double, _dp, _ip, _i64p]
+                _dp, ctypes.c_int, ctypes.c_int, _u8p, ctypes.c_int, _ip, ctypes.c_double, _dp, _ip, _i64p, _dp]
             lib.oracle_render_sums.restype = ctypes.c_int
             lib.oracle_compose.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
             lib.oracle_compose.restype = ctypes.c_int
             lib.oracle_backward.argtypes = params + [
-                _dp, _dp, ctypes.c_int, ctypes.c_int, _u8p, _dp, _dp, _ip, ctypes.c_double, _dp, _dp, _u8p]
+                _dp, _dp, ctypes.c_int, ctypes.c_int, _u8p, _dp, _dp, _ip, ctypes.c_double, _dp, _dp, _u8p, _dp]
             lib.oracle_backward.restype = ctypes.c_int
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
@@ -136,10 +136,13 @@ def project(scene, cam):
     return out
 
 
-def render_sums(scene, cam, subset=None, brute=False, window=None, amb_band=0.0, want_amb=False):
+def render_sums(scene, cam, subset=None, brute=False, window=None, amb_band=0.0, want_amb=False,
+                amb_sums=None):
     """Per-pixel sums (P_r, P_g, P_b, Q, log T) of the selected splats, float64 [5, H, W].
 
     Returns (sums, amb_pixel or None, stats) where stats = (contributing pairs, clamped pairs).
+    amb_sums (optional float64 [3, H, W]) receives, over the pairs within amb_band of the 1/255
+    cut, sum a/(1-a), sum a w and sum a w max_c c.
     """
     lib = _load()
     n, a = _splat_args(scene)
@@ -150,9 +153,11 @@ def render_sums(scene, cam, subset=None, brute=False, window=None, amb_band=0.0,
     m = _mask(subset, n)
     win = _window(window)
     c = _cam16(cam)
+    if amb_sums is not None:
+        assert amb_sums.dtype == np.float64 and amb_sums.shape == (3, H, W) and amb_sums.flags.c_contiguous
     rc = lib.oracle_render_sums(n, *[_ptr(x) for x in a], float(scene["sigma"]), _ptr(c), W, H,
                                 _ptr(m, _u8p), int(bool(brute)), _ptr(win, _ip), float(amb_band),
-                                _ptr(sums), _ptr(amb, _ip), _ptr(stats, _i64p))
+                                _ptr(sums), _ptr(amb, _ip), _ptr(stats, _i64p), _ptr(amb_sums))
     if rc != 0:
         raise MemoryError("oracle_render_sums failed")
     return sums, amb, (int(stats[0]), int(stats[1]))
@@ -170,31 +175,52 @@ def compose(sums, bg):
     return img, aux
 
 
-def render(scene, cam, subset=None, frozen_sums=None, brute=False, window=None, amb_band=0.0):
+def render(scene, cam, subset=None, frozen_sums=None, brute=False, window=None, amb_band=0.0,
+           frozen_amb_sums=None):
     """Image of the selected splats plus optional extra sums (e.g. a frozen complement).
 
-    Returns dict(image [H,W,3], sums [5,H,W] (total), amb [H,W] int32, pairs, clamped).
+    Returns dict(image [H,W,3], sums [5,H,W] (total), amb [H,W] int32, flip [H,W], pairs, clamped).
+    flip bounds, to first order, how far the pairs within amb_band of the 1/255 cut can move the
+    pixel's colour (in any channel) if included or dropped:
+        T max|F - c0| sum a/(1-a) + (1 - T)/Q (sum a w max c + max|F| sum a w),
+    and (1 - T) (max c + max|F|) where those pairs hold at least half of Q.
+    frozen_amb_sums adds the same sums of a frozen complement rendered separately.
     """
-    sums, amb, (pairs, clamped) = render_sums(scene, cam, subset, brute, window, amb_band, True)
+    W, H = int(cam["width"]), int(cam["height"])
+    ab = np.zeros((3, H, W))
+    sums, amb, (pairs, clamped) = render_sums(scene, cam, subset, brute, window, amb_band, True, ab)
     if frozen_sums is not None:
         sums = sums + _f64(frozen_sums)
+    if frozen_amb_sums is not None:
+        ab = ab + _f64(frozen_amb_sums)
     img, aux = compose(sums, scene["bg"])
-    return dict(image=img, sums=sums, aux=aux, amb=amb, pairs=pairs, clamped=clamped)
+    F, T, Q = aux[..., :3], aux[..., 3], aux[..., 4]
+    bg = _f64(scene["bg"]).reshape(3)
+    fmax = np.abs(F).max(axis=2)
+    fc0 = np.abs(F - bg).max(axis=2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        flip = T * fc0 * ab[0] + np.where(Q > 0, (1 - T) / np.where(Q > 0, Q, 1) * (ab[2] + fmax * ab[1]), 0.0)
+    heavy = ab[1] >= 0.5 * Q
+    cmax = np.where(ab[1] > 0, ab[2] / np.where(ab[1] > 0, ab[1], 1), 0.0)
+    flip = np.where(heavy & (ab[1] > 0), np.maximum(flip, (1 - T) * (cmax + fmax)), flip)
+    return dict(image=img, sums=sums, aux=aux, amb=amb, flip=flip, pairs=pairs, clamped=clamped)
 
 
-def backward(scene, cam, sums_total, dL_dC, active=None, window=None, amb_band=0.0, with_scale=False):
+def backward_full(scene, cam, sums_total, dL_dC, active=None, window=None, amb_band=0.0, want_flip=False):
     """Analytic gradient of L = sum dL_dC . C (Eq. 10 chained to all parameters).
 
-    Returns (grads [N,75] with unselected rows NaN, dL/dsigma, amb_splat [N] uint8), and with
-    with_scale=True a fourth value: the sum of |per-splat dL/dsigma terms|.
-    """
+    Returns dict(grads [N,75] (unselected rows NaN), dsigma, dsigma_scale (sum of |per-splat terms|),
+    amb [N] uint8 (bit 0: a pair near the 1/255 cut or the 0.99 clamp; bit 1: a max(0,.) kink or the
+    near plane within amb_band), flip [N,75] (sum over the bit-0 pairs of |that pair's gradient|,
+    with want_flip) and dsigma_flip)."""
     lib = _load()
     n, a = _splat_args(scene)
     W, H = int(cam["width"]), int(cam["height"])
     s = _f64(sums_total).reshape(5, H, W)
     g = _f64(dL_dC).reshape(H, W, 3)
     grads = np.full((n, NPARAM), np.nan)
-    dsig = np.zeros(2)
+    flip = np.zeros((n, NPARAM)) if want_flip else None
+    dsig = np.zeros(3)
     amb = np.zeros(n, dtype=np.uint8)
     m = _mask(active, n)
     win = _window(window)
@@ -202,7 +228,19 @@ def backward(scene, cam, sums_total, dL_dC, active=None, window=None, amb_band=0
     c = _cam16(cam)
     lib.oracle_backward(n, *[_ptr(x) for x in a], float(scene["sigma"]), _ptr(b), _ptr(c), W, H,
                         _ptr(m, _u8p), _ptr(s), _ptr(g), _ptr(win, _ip), float(amb_band),
-                        _ptr(grads), _ptr(dsig), _ptr(amb, _u8p))
+                        _ptr(grads), _ptr(dsig), _ptr(amb, _u8p), _ptr(flip))
+    return dict(grads=grads, dsigma=float(dsig[0]), dsigma_scale=float(dsig[1]), dsigma_flip=float(dsig[2]),
+                amb=amb, flip=flip)
+
+
+def backward(scene, cam, sums_total, dL_dC, active=None, window=None, amb_band=0.0, with_scale=False):
+    """Analytic gradient of L = sum dL_dC . C (Eq. 10 chained to all parameters).
+
+    Returns (grads [N,75] with unselected rows NaN, dL/dsigma, amb_splat [N] uint8 (nonzero: some
+    ambiguity within amb_band, see backward_full)), and with with_scale=True a fourth value: the
+    sum of |per-splat dL/dsigma terms|.
+    """
+    r = backward_full(scene, cam, sums_total, dL_dC, active, window, amb_band)
     if with_scale:
-        return grads, float(dsig[0]), amb, float(dsig[1])
-    return grads, float(dsig[0]), amb
+        return r["grads"], r["dsigma"], r["amb"], r["dsigma_scale"]
+    return r["grads"], r["dsigma"], r["amb"]

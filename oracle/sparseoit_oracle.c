@@ -331,17 +331,22 @@ static void clip_window(const int *window, int W, int H, int *wx0, int *wy0, int
  * `window` (x0, y0, x1, y1, half-open; NULL = whole view) are computed, the
  * rest of `sums` is zero.  amb_pixel (optional, [HW]) counts the pairs whose
  * unclamped alpha lies within a factor exp(amb_band) of the 1/255 threshold.
+ * amb_sums (optional, [3][HW]) accumulates over those pairs sum a/(1 - a),
+ * sum a w and sum a w max_c c (a = the unclamped alpha): enough to bound
+ * how much adding or dropping them can move the composed colour.
  * stats (optional, [2]) = number of contributing (splat, pixel) pairs and of
  * pairs clamped at 0.99. */
 int oracle_render_sums(int64_t n, const double *means, const double *quats, const double *log_scales,
                        const double *opacity_logits, const double *sh_color, const double *sh_weight,
                        double sigma, const double *cam_in, int W, int H, const uint8_t *subset, int brute,
-                       const int *window, double amb_band, double *sums, int32_t *amb_pixel, int64_t *stats) {
+                       const int *window, double amb_band, double *sums, int32_t *amb_pixel, int64_t *stats,
+                       double *amb_sums) {
     ocam cam;
     load_camera(cam_in, &cam);
     const int64_t HW = (int64_t)W * H;
     memset(sums, 0, 5 * HW * sizeof(double));
     if (amb_pixel) memset(amb_pixel, 0, HW * sizeof(int32_t));
+    if (amb_sums) memset(amb_sums, 0, 3 * HW * sizeof(double));
     int wx0, wy0, wx1, wy1;
     clip_window(window, W, H, &wx0, &wy0, &wx1, &wy1);
     if (wx1 <= wx0 || wy1 <= wy0) { if (stats) { stats[0] = 0; stats[1] = 0; } return 0; }
@@ -387,6 +392,7 @@ int oracle_render_sums(int64_t n, const double *means, const double *quats, cons
             const int64_t pix = (int64_t)y * W + x;
             const double px = x + 0.5, py = y + 0.5;
             double Pr = 0, Pg = 0, Pb = 0, Q = 0, lT = 0;
+            double ab0 = 0, ab1 = 0, ab2 = 0;
             int amb = 0;
             for (int64_t e = lo; e < hi; ++e) {
                 const int64_t i = brute ? e : lists[e];
@@ -394,7 +400,14 @@ int oracle_render_sums(int64_t n, const double *means, const double *quats, cons
                 if (!P->valid) continue;
                 if (!brute && (x < P->x0 || x > P->x1 || y < P->y0 || y > P->y1)) continue;
                 double ar = pair_alpha_raw(P, px, py, NULL, NULL, NULL);
-                if (near_log(ar, OR_ALPHA_MIN, amb_band)) amb++;
+                if (near_log(ar, OR_ALPHA_MIN, amb_band)) {
+                    amb++;
+                    double cm = P->c[0] > P->c[1] ? P->c[0] : P->c[1];
+                    cm = cm > P->c[2] ? cm : P->c[2];
+                    ab0 += ar / (1.0 - ar);
+                    ab1 += ar * P->w;
+                    ab2 += ar * P->w * cm;
+                }
                 if (ar < OR_ALPHA_MIN) continue;
                 double a = ar < OR_ALPHA_MAX ? ar : OR_ALPHA_MAX;
                 if (ar > OR_ALPHA_MAX) n_clamped++;
@@ -412,6 +425,11 @@ int oracle_render_sums(int64_t n, const double *means, const double *quats, cons
             sums[3 * HW + pix] = Q;
             sums[4 * HW + pix] = lT;
             if (amb_pixel) amb_pixel[pix] = amb;
+            if (amb_sums) {
+                amb_sums[0 * HW + pix] = ab0;
+                amb_sums[1 * HW + pix] = ab1;
+                amb_sums[2 * HW + pix] = ab2;
+            }
         }
     }
     if (stats) { stats[0] = n_pairs; stats[1] = n_clamped; }
@@ -441,6 +459,173 @@ int oracle_compose(int W, int H, const double *sums, const double *bg, double *i
 
 /* -------------------------------------------------------- backward ---- */
 
+/* Screen-space accumulators of one splat: dL/dmu' (2), dL/dK (K00, K01 = K10,
+ * K11), dL/do, dL/dc (3), dL/dw. */
+typedef struct {
+    double m2[2], K[3], o, c[3], w;
+} screen_grads;
+
+/* Eq. 10 contracted with g = dL/dC at one pixel (state T, F, Q), for the pair
+ * with unclamped alpha ar at offset (dx, dy), exponent p; added to *sg.
+ * The alpha path (o, mu', K) is skipped where alpha is clamped at 0.99. */
+static void pair_screen_grads(const oproj *P, double ar, double dx, double dy, double p, double T, const double F[3],
+                              double Q, const double g[3], const double *bg, screen_grads *sg) {
+    double a = ar < OR_ALPHA_MAX ? ar : OR_ALPHA_MAX;
+    double invQ = Q > 0.0 ? 1.0 / Q : 0.0;
+    double dLda = 0.0, dLdw = 0.0;
+    for (int ch = 0; ch < 3; ++ch) {
+        double dCdc = (1.0 - T) * a * P->w * invQ;
+        double dCda = T / (1.0 - a) * (F[ch] - bg[ch]) + (1.0 - T) * P->w * invQ * (P->c[ch] - F[ch]);
+        double dCdw = (1.0 - T) * a * invQ * (P->c[ch] - F[ch]);
+        sg->c[ch] += g[ch] * dCdc;
+        dLda += g[ch] * dCda;
+        dLdw += g[ch] * dCdw;
+    }
+    sg->w += dLdw;
+    if (ar <= OR_ALPHA_MAX) {
+        /* a = o exp(-p): da/do = exp(-p), da/dp = -a;
+         * p = 1/2 d^T K d: dp/dmu' = -K d, dp/dK = 1/2 d d^T */
+        sg->o += dLda * exp(-p);
+        double dLdp = -dLda * a;
+        sg->m2[0] += dLdp * -(P->con[0] * dx + P->con[1] * dy);
+        sg->m2[1] += dLdp * -(P->con[1] * dx + P->con[2] * dy);
+        sg->K[0] += dLdp * 0.5 * dx * dx;
+        sg->K[1] += dLdp * 0.5 * dx * dy;
+        sg->K[2] += dLdp * 0.5 * dy * dy;
+    }
+}
+
+/* Chain the screen-space gradients of splat P to its 75 parameters (gout,
+ * overwritten) and to sigma (*dsig, overwritten): Eq. 6 (EWA projection and
+ * the inverse), Eq. 1 (weight), Eq. 4 (SH colour / weight and the view
+ * direction), Sec. 3.1 (sigmoid opacity), Eq. 2 (covariance from quaternion
+ * and scales). */
+static void chain_to_params(const oproj *P, const ocam *cam, const double *h, const double *hw, double sigma,
+                            const screen_grads *sg, double *gout, double *dsig) {
+    memset(gout, 0, OR_NPARAM * sizeof(double));
+    *dsig = 0.0;
+    /* K = Sigma'^-1: dL/dSigma' = -K G K with G the symmetric gradient in K */
+    const double K[4] = {P->con[0], P->con[1], P->con[1], P->con[2]};
+    const double G[4] = {sg->K[0], sg->K[1], sg->K[1], sg->K[2]};
+    double KG[4], Gs[4];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) KG[2 * a + b] = K[2 * a + 0] * G[0 * 2 + b] + K[2 * a + 1] * G[1 * 2 + b];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) Gs[2 * a + b] = -(KG[2 * a + 0] * K[0 * 2 + b] + KG[2 * a + 1] * K[1 * 2 + b]);
+    /* Sigma' = T Sigma T^T + 0.3 I, T = J W:
+     *   dL/dSigma = T^T Gs T,  dL/dT = 2 Gs T Sigma */
+    double gSig[9], gT[6];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double acc = 0.0;
+            for (int k = 0; k < 2; ++k)
+                for (int l = 0; l < 2; ++l) acc += P->Tm[3 * k + a] * Gs[2 * k + l] * P->Tm[3 * l + b];
+            gSig[3 * a + b] = acc;
+        }
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double acc = 0.0;
+            for (int k = 0; k < 2; ++k)
+                for (int l = 0; l < 3; ++l) acc += 2.0 * Gs[2 * a + k] * P->Tm[3 * k + l] * P->Sig[3 * l + b];
+            gT[3 * a + b] = acc;
+        }
+    /* T = J W: dL/dJ = dL/dT W^T */
+    double gJ[6];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += gT[3 * a + k] * cam->R[3 * b + k];
+            gJ[3 * a + b] = acc;
+        }
+    const double x = P->t[0], y = P->t[1], z = P->t[2], fx = cam->fx, fy = cam->fy;
+    double gt[3] = {0, 0, 0};
+    /* J entries as functions of t */
+    gt[0] += gJ[2] * (-fx / (z * z));
+    gt[1] += gJ[5] * (-fy / (z * z));
+    gt[2] += gJ[0] * (-fx / (z * z)) + gJ[2] * (2.0 * fx * x / (z * z * z)) + gJ[4] * (-fy / (z * z)) +
+             gJ[5] * (2.0 * fy * y / (z * z * z));
+    /* mu' = (fx x/z + cx, fy y/z + cy) */
+    gt[0] += sg->m2[0] * fx / z;
+    gt[1] += sg->m2[1] * fy / z;
+    gt[2] += -sg->m2[0] * fx * x / (z * z) - sg->m2[1] * fy * y / (z * z);
+    /* Eq. 1: w = max(0, 1 - z/sigma) v */
+    double g_v = 0.0;
+    if (P->zterm > 0.0) {
+        g_v = sg->w * P->zterm;
+        gt[2] += sg->w * P->v * (-1.0 / sigma);
+        *dsig = sg->w * P->v * z / (sigma * sigma);
+    }
+    /* Eq. 4 colour and weight SH */
+    double Yb[16], dY[48];
+    oracle_sh_basis(P->n, Yb, dY);
+    double g_n[3] = {0, 0, 0};
+    for (int ch = 0; ch < 3; ++ch) {
+        if (!(P->c_raw[ch] > 0.0)) continue;
+        for (int k = 0; k < 16; ++k) {
+            gout[11 + 3 * k + ch] = sg->c[ch] * Yb[k];
+            for (int e = 0; e < 3; ++e) g_n[e] += sg->c[ch] * h[3 * k + ch] * dY[3 * k + e];
+        }
+    }
+    if (P->v_raw > 0.0) {
+        for (int k = 0; k < 16; ++k) {
+            gout[59 + k] = g_v * Yb[k];
+            for (int e = 0; e < 3; ++e) g_n[e] += g_v * hw[k] * dY[3 * k + e];
+        }
+    }
+    /* mean: t = R_w mu + t_w, n = (mu - pos)/|mu - pos| */
+    double ndot = P->n[0] * g_n[0] + P->n[1] * g_n[1] + P->n[2] * g_n[2];
+    for (int e = 0; e < 3; ++e) {
+        double acc = cam->R[0 * 3 + e] * gt[0] + cam->R[1 * 3 + e] * gt[1] + cam->R[2 * 3 + e] * gt[2];
+        acc += (g_n[e] - P->n[e] * ndot) / P->dlen;
+        gout[e] = acc;
+    }
+    /* opacity: o = sigmoid(l) */
+    gout[10] = sg->o * P->o * (1.0 - P->o);
+    /* Eq. 2: Sigma = M M^T, M = R S: dL/dM = 2 dL/dSigma M */
+    double M[9], gM[9];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) M[3 * a + b] = P->Rq[3 * a + b] * P->s[b];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += (gSig[3 * a + k] + gSig[3 * k + a]) * M[3 * k + b];
+            gM[3 * a + b] = acc;
+        }
+    double gR[9];
+    for (int b = 0; b < 3; ++b) {
+        double gs = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            gs += gM[3 * a + b] * P->Rq[3 * a + b];
+            gR[3 * a + b] = gM[3 * a + b] * P->s[b];
+        }
+        gout[7 + b] = gs * P->s[b];
+    }
+    /* R(q^): partial derivatives of each entry in (a, b, c, d) = (w, x, y, z) */
+    const double qa = P->qn[0], qb = P->qn[1], qc = P->qn[2], qd = P->qn[3];
+    double gq[4] = {0, 0, 0, 0};
+    /* R00 = 1 - 2(c^2 + d^2) */
+    gq[2] += gR[0] * (-4.0 * qc); gq[3] += gR[0] * (-4.0 * qd);
+    /* R01 = 2(bc - ad) */
+    gq[0] += gR[1] * (-2.0 * qd); gq[1] += gR[1] * (2.0 * qc); gq[2] += gR[1] * (2.0 * qb); gq[3] += gR[1] * (-2.0 * qa);
+    /* R02 = 2(bd + ac) */
+    gq[0] += gR[2] * (2.0 * qc); gq[1] += gR[2] * (2.0 * qd); gq[2] += gR[2] * (2.0 * qa); gq[3] += gR[2] * (2.0 * qb);
+    /* R10 = 2(bc + ad) */
+    gq[0] += gR[3] * (2.0 * qd); gq[1] += gR[3] * (2.0 * qc); gq[2] += gR[3] * (2.0 * qb); gq[3] += gR[3] * (2.0 * qa);
+    /* R11 = 1 - 2(b^2 + d^2) */
+    gq[1] += gR[4] * (-4.0 * qb); gq[3] += gR[4] * (-4.0 * qd);
+    /* R12 = 2(cd - ab) */
+    gq[0] += gR[5] * (-2.0 * qb); gq[1] += gR[5] * (-2.0 * qa); gq[2] += gR[5] * (2.0 * qd); gq[3] += gR[5] * (2.0 * qc);
+    /* R20 = 2(bd - ac) */
+    gq[0] += gR[6] * (-2.0 * qc); gq[1] += gR[6] * (2.0 * qd); gq[2] += gR[6] * (-2.0 * qa); gq[3] += gR[6] * (2.0 * qb);
+    /* R21 = 2(cd + ab) */
+    gq[0] += gR[7] * (2.0 * qb); gq[1] += gR[7] * (2.0 * qa); gq[2] += gR[7] * (2.0 * qd); gq[3] += gR[7] * (2.0 * qc);
+    /* R22 = 1 - 2(b^2 + c^2) */
+    gq[1] += gR[8] * (-4.0 * qb); gq[2] += gR[8] * (-4.0 * qc);
+    /* q^ = q / |q| */
+    double qdot = qa * gq[0] + qb * gq[1] + qc * gq[2] + qd * gq[3];
+    for (int k = 0; k < 4; ++k) gout[3 + k] = (gq[k] - P->qn[k] * qdot) / P->qlen;
+}
+
 /* Gradient of L = sum_pixels dL_dC . C with respect to every parameter of
  * the splats selected by `active` (NULL = all), for the image composed from
  * `sums_total` (the sums of ALL splats, e.g. active + frozen).  Only pixels
@@ -449,13 +634,18 @@ int oracle_compose(int W, int H, const double *sums, const double *bg, double *i
  * grads[n, 75] rows of selected splats are overwritten, the others are not
  * touched.  Row layout: mean (3), quaternion (4), log-scale (3),
  * opacity logit (1), colour SH [16][3] (48), weight SH (16).
- * dsigma (optional, [2]) = dL/dsigma summed over the selected splats and
- * the sum of the absolute values of those per-splat terms (the scale a
- * rounding error of the sum is measured against).
- * amb_splat (optional, [n]) is set to 1 for a selected splat that has a pair
- * whose unclamped alpha is within exp(amb_band) of 1/255 or of 0.99, a
- * colour / weight SH value within amb_band of the max(0,.) kink, or
- * |1 - t_z/sigma| < amb_band; 0 otherwise.
+ * dsigma (optional, [3]) = dL/dsigma summed over the selected splats, the
+ * sum of the absolute values of those per-splat terms (the scale a rounding
+ * error of the sum is measured against), and the allowance of the near-cut
+ * pairs for dL/dsigma (see flip).
+ * amb_splat (optional, [n]) for a selected splat: bit 0 set if a pair's
+ * unclamped alpha is within exp(amb_band) of 1/255 or of 0.99; bit 1 set if
+ * a colour / weight SH value is within amb_band of the max(0,.) kink,
+ * |1 - t_z/sigma| < amb_band or |t_z - 0.2| < amb_band (near plane).
+ * flip (optional, [n, 75]) for a selected splat: the sum over its bit-0
+ * pairs of |the parameter gradient of that pair alone| (each taken as
+ * included and unclamped) -- how far a different inclusion / clamping
+ * decision on those pairs can move its gradient.
  *
  * Per pair the derivatives of Eq. 10 are used as printed:
  *   dC/dc_i     = (1-T) a_i w_i / Q
@@ -466,43 +656,47 @@ int oracle_backward(int64_t n, const double *means, const double *quats, const d
                     const double *opacity_logits, const double *sh_color, const double *sh_weight, double sigma,
                     const double *bg, const double *cam_in, int W, int H, const uint8_t *active,
                     const double *sums_total, const double *dL_dC, const int *window, double amb_band,
-                    double *grads, double *dsigma, uint8_t *amb_splat) {
+                    double *grads, double *dsigma, uint8_t *amb_splat, double *flip) {
     ocam cam;
     load_camera(cam_in, &cam);
     const int64_t HW = (int64_t)W * H;
     int wx0, wy0, wx1, wy1;
     clip_window(window, W, H, &wx0, &wy0, &wx1, &wy1);
     double slack = (amb_band > 1e-6 ? amb_band : 1e-6) + 1e-9;
-    double dsig_total = 0.0, dsig_abs = 0.0;
+    double dsig_total = 0.0, dsig_abs = 0.0, dsig_flip = 0.0;
 
-#pragma omp parallel for schedule(dynamic, 64) reduction(+ : dsig_total, dsig_abs)
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : dsig_total, dsig_abs, dsig_flip)
     for (int64_t i = 0; i < n; ++i) {
         if (active && !active[i]) continue;
         double *gout = grads + (int64_t)OR_NPARAM * i;
+        double *fout = flip ? flip + (int64_t)OR_NPARAM * i : NULL;
         memset(gout, 0, OR_NPARAM * sizeof(double));
+        if (fout) memset(fout, 0, OR_NPARAM * sizeof(double));
         if (amb_splat) amb_splat[i] = 0;
         oproj P;
         project_one(i, means, quats, log_scales, opacity_logits, sh_color, sh_weight, sigma, &cam, W, H, slack, &P);
-        if (amb_splat && amb_band > 0.0 && fabs(P.t[2] - OR_NEAR_Z) < amb_band) amb_splat[i] = 1;
-        if (!P.valid) continue;
-        int amb = amb_splat ? amb_splat[i] : 0;
-        if (amb_band > 0.0) {
-            for (int ch = 0; ch < 3; ++ch) if (fabs(P.c_raw[ch]) < amb_band) amb = 1;
-            if (fabs(P.v_raw) < amb_band || fabs(P.zterm) < amb_band) amb = 1;
+        int amb = 0;
+        if (amb_band > 0.0 && fabs(P.t[2] - OR_NEAR_Z) < amb_band) amb |= 2;
+        if (!P.valid) {
+            if (amb_splat) amb_splat[i] = (uint8_t)amb;
+            continue;
         }
-        /* screen-space accumulators */
-        double g_m2[2] = {0, 0}, g_K[3] = {0, 0, 0} /* d/dK00, d/dK01 (= d/dK10), d/dK11 */;
-        double g_o = 0, g_c[3] = {0, 0, 0}, g_w = 0;
+        if (amb_band > 0.0) {
+            for (int ch = 0; ch < 3; ++ch) if (fabs(P.c_raw[ch]) < amb_band) amb |= 2;
+            if (fabs(P.v_raw) < amb_band || fabs(P.zterm) < amb_band) amb |= 2;
+        }
+        const double *h = sh_color + 48 * i, *hw = sh_weight + 16 * i;
+        screen_grads sg;
+        memset(&sg, 0, sizeof(sg));
         int x0 = P.x0 > wx0 ? P.x0 : wx0, x1 = P.x1 < wx1 - 1 ? P.x1 : wx1 - 1;
         int y0 = P.y0 > wy0 ? P.y0 : wy0, y1 = P.y1 < wy1 - 1 ? P.y1 : wy1 - 1;
         for (int y = y0; y <= y1; ++y) {
             for (int x = x0; x <= x1; ++x) {
                 double dx, dy, p;
                 double ar = pair_alpha_raw(&P, x + 0.5, y + 0.5, &dx, &dy, &p);
-                if (near_log(ar, OR_ALPHA_MIN, amb_band) || near_log(ar, OR_ALPHA_MAX, amb_band)) amb = 1;
-                if (ar < OR_ALPHA_MIN) continue;
+                const int near = near_log(ar, OR_ALPHA_MIN, amb_band) || near_log(ar, OR_ALPHA_MAX, amb_band);
+                if (ar < OR_ALPHA_MIN && !near) continue;
                 const int64_t pix = (int64_t)y * W + x;
-                double a = ar < OR_ALPHA_MAX ? ar : OR_ALPHA_MAX;
                 double Q = sums_total[3 * HW + pix];
                 double T = exp(sums_total[4 * HW + pix]);
                 double F[3], g[3];
@@ -510,156 +704,30 @@ int oracle_backward(int64_t n, const double *means, const double *quats, const d
                     F[ch] = Q > 0.0 ? sums_total[ch * HW + pix] / Q : 0.0;
                     g[ch] = dL_dC[3 * pix + ch];
                 }
-                double invQ = Q > 0.0 ? 1.0 / Q : 0.0;
-                double dLda = 0.0, dLdw = 0.0;
-                for (int ch = 0; ch < 3; ++ch) {
-                    double dCdc = (1.0 - T) * a * P.w * invQ;
-                    double dCda = T / (1.0 - a) * (F[ch] - bg[ch]) + (1.0 - T) * P.w * invQ * (P.c[ch] - F[ch]);
-                    double dCdw = (1.0 - T) * a * invQ * (P.c[ch] - F[ch]);
-                    g_c[ch] += g[ch] * dCdc;
-                    dLda += g[ch] * dCda;
-                    dLdw += g[ch] * dCdw;
-                }
-                g_w += dLdw;
-                if (ar <= OR_ALPHA_MAX) {
-                    /* a = o exp(-p): da/do = exp(-p), da/dp = -a;
-                     * p = 1/2 d^T K d: dp/dmu' = -K d, dp/dK = 1/2 d d^T */
-                    g_o += dLda * exp(-p);
-                    double dLdp = -dLda * a;
-                    g_m2[0] += dLdp * -(P.con[0] * dx + P.con[1] * dy);
-                    g_m2[1] += dLdp * -(P.con[1] * dx + P.con[2] * dy);
-                    g_K[0] += dLdp * 0.5 * dx * dx;
-                    g_K[1] += dLdp * 0.5 * dx * dy;
-                    g_K[2] += dLdp * 0.5 * dy * dy;
+                if (ar >= OR_ALPHA_MIN) pair_screen_grads(&P, ar, dx, dy, p, T, F, Q, g, bg, &sg);
+                if (near) {
+                    amb |= 1;
+                    if (fout) {
+                        /* this pair alone, taken as included and unclamped */
+                        screen_grads one;
+                        memset(&one, 0, sizeof(one));
+                        double ar1 = ar < OR_ALPHA_MAX ? (ar > OR_ALPHA_MIN ? ar : OR_ALPHA_MIN) : OR_ALPHA_MAX;
+                        pair_screen_grads(&P, ar1, dx, dy, p, T, F, Q, g, bg, &one);
+                        double g1[OR_NPARAM], s1;
+                        chain_to_params(&P, &cam, h, hw, sigma, &one, g1, &s1);
+                        for (int k = 0; k < OR_NPARAM; ++k) fout[k] += fabs(g1[k]);
+                        dsig_flip += fabs(s1);
+                    }
                 }
             }
         }
         if (amb_splat) amb_splat[i] = (uint8_t)amb;
-
-        /* K = Sigma'^-1: dL/dSigma' = -K G K with G the symmetric gradient in K */
-        const double K[4] = {P.con[0], P.con[1], P.con[1], P.con[2]};
-        const double G[4] = {g_K[0], g_K[1], g_K[1], g_K[2]};
-        double KG[4], Gs[4];
-        for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b) KG[2 * a + b] = K[2 * a + 0] * G[0 * 2 + b] + K[2 * a + 1] * G[1 * 2 + b];
-        for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b) Gs[2 * a + b] = -(KG[2 * a + 0] * K[0 * 2 + b] + KG[2 * a + 1] * K[1 * 2 + b]);
-        /* Sigma' = T Sigma T^T + 0.3 I, T = J W:
-         *   dL/dSigma = T^T Gs T,  dL/dT = 2 Gs T Sigma */
-        double gSig[9], gT[6];
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) {
-                double acc = 0.0;
-                for (int k = 0; k < 2; ++k)
-                    for (int l = 0; l < 2; ++l) acc += P.Tm[3 * k + a] * Gs[2 * k + l] * P.Tm[3 * l + b];
-                gSig[3 * a + b] = acc;
-            }
-        for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 3; ++b) {
-                double acc = 0.0;
-                for (int k = 0; k < 2; ++k)
-                    for (int l = 0; l < 3; ++l) acc += 2.0 * Gs[2 * a + k] * P.Tm[3 * k + l] * P.Sig[3 * l + b];
-                gT[3 * a + b] = acc;
-            }
-        /* T = J W: dL/dJ = dL/dT W^T */
-        double gJ[6];
-        for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 3; ++b) {
-                double acc = 0.0;
-                for (int k = 0; k < 3; ++k) acc += gT[3 * a + k] * cam.R[3 * b + k];
-                gJ[3 * a + b] = acc;
-            }
-        const double x = P.t[0], y = P.t[1], z = P.t[2], fx = cam.fx, fy = cam.fy;
-        double gt[3] = {0, 0, 0};
-        /* J entries as functions of t */
-        gt[0] += gJ[2] * (-fx / (z * z));
-        gt[1] += gJ[5] * (-fy / (z * z));
-        gt[2] += gJ[0] * (-fx / (z * z)) + gJ[2] * (2.0 * fx * x / (z * z * z)) + gJ[4] * (-fy / (z * z)) +
-                 gJ[5] * (2.0 * fy * y / (z * z * z));
-        /* mu' = (fx x/z + cx, fy y/z + cy) */
-        gt[0] += g_m2[0] * fx / z;
-        gt[1] += g_m2[1] * fy / z;
-        gt[2] += -g_m2[0] * fx * x / (z * z) - g_m2[1] * fy * y / (z * z);
-        /* Eq. 1: w = max(0, 1 - z/sigma) v */
-        double g_v = 0.0;
-        if (P.zterm > 0.0) {
-            g_v = g_w * P.zterm;
-            gt[2] += g_w * P.v * (-1.0 / sigma);
-            dsig_total += g_w * P.v * z / (sigma * sigma);
-            dsig_abs += fabs(g_w * P.v * z / (sigma * sigma));
-        }
-        /* Eq. 4 colour and weight SH */
-        double Yb[16], dY[48];
-        oracle_sh_basis(P.n, Yb, dY);
-        double g_n[3] = {0, 0, 0};
-        const double *h = sh_color + 48 * i, *hw = sh_weight + 16 * i;
-        for (int ch = 0; ch < 3; ++ch) {
-            if (!(P.c_raw[ch] > 0.0)) continue;
-            for (int k = 0; k < 16; ++k) {
-                gout[11 + 3 * k + ch] = g_c[ch] * Yb[k];
-                for (int e = 0; e < 3; ++e) g_n[e] += g_c[ch] * h[3 * k + ch] * dY[3 * k + e];
-            }
-        }
-        if (P.v_raw > 0.0) {
-            for (int k = 0; k < 16; ++k) {
-                gout[59 + k] = g_v * Yb[k];
-                for (int e = 0; e < 3; ++e) g_n[e] += g_v * hw[k] * dY[3 * k + e];
-            }
-        }
-        /* mean: t = R_w mu + t_w, n = (mu - pos)/|mu - pos| */
-        double ndot = P.n[0] * g_n[0] + P.n[1] * g_n[1] + P.n[2] * g_n[2];
-        for (int e = 0; e < 3; ++e) {
-            double acc = cam.R[0 * 3 + e] * gt[0] + cam.R[1 * 3 + e] * gt[1] + cam.R[2 * 3 + e] * gt[2];
-            acc += (g_n[e] - P.n[e] * ndot) / P.dlen;
-            gout[e] = acc;
-        }
-        /* opacity: o = sigmoid(l) */
-        gout[10] = g_o * P.o * (1.0 - P.o);
-        /* Eq. 2: Sigma = M M^T, M = R S: dL/dM = 2 dL/dSigma M */
-        double M[9], gM[9];
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) M[3 * a + b] = P.Rq[3 * a + b] * P.s[b];
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) {
-                double acc = 0.0;
-                for (int k = 0; k < 3; ++k) acc += (gSig[3 * a + k] + gSig[3 * k + a]) * M[3 * k + b];
-                gM[3 * a + b] = acc;
-            }
-        double gR[9];
-        for (int b = 0; b < 3; ++b) {
-            double gs = 0.0;
-            for (int a = 0; a < 3; ++a) {
-                gs += gM[3 * a + b] * P.Rq[3 * a + b];
-                gR[3 * a + b] = gM[3 * a + b] * P.s[b];
-            }
-            gout[7 + b] = gs * P.s[b];
-        }
-        /* R(q^): partial derivatives of each entry in (a, b, c, d) = (w, x, y, z) */
-        const double qa = P.qn[0], qb = P.qn[1], qc = P.qn[2], qd = P.qn[3];
-        double gq[4] = {0, 0, 0, 0};
-        /* R00 = 1 - 2(c^2 + d^2) */
-        gq[2] += gR[0] * (-4.0 * qc); gq[3] += gR[0] * (-4.0 * qd);
-        /* R01 = 2(bc - ad) */
-        gq[0] += gR[1] * (-2.0 * qd); gq[1] += gR[1] * (2.0 * qc); gq[2] += gR[1] * (2.0 * qb); gq[3] += gR[1] * (-2.0 * qa);
-        /* R02 = 2(bd + ac) */
-        gq[0] += gR[2] * (2.0 * qc); gq[1] += gR[2] * (2.0 * qd); gq[2] += gR[2] * (2.0 * qa); gq[3] += gR[2] * (2.0 * qb);
-        /* R10 = 2(bc + ad) */
-        gq[0] += gR[3] * (2.0 * qd); gq[1] += gR[3] * (2.0 * qc); gq[2] += gR[3] * (2.0 * qb); gq[3] += gR[3] * (2.0 * qa);
-        /* R11 = 1 - 2(b^2 + d^2) */
-        gq[1] += gR[4] * (-4.0 * qb); gq[3] += gR[4] * (-4.0 * qd);
-        /* R12 = 2(cd - ab) */
-        gq[0] += gR[5] * (-2.0 * qb); gq[1] += gR[5] * (-2.0 * qa); gq[2] += gR[5] * (2.0 * qd); gq[3] += gR[5] * (2.0 * qc);
-        /* R20 = 2(bd - ac) */
-        gq[0] += gR[6] * (-2.0 * qc); gq[1] += gR[6] * (2.0 * qd); gq[2] += gR[6] * (-2.0 * qa); gq[3] += gR[6] * (2.0 * qb);
-        /* R21 = 2(cd + ab) */
-        gq[0] += gR[7] * (2.0 * qb); gq[1] += gR[7] * (2.0 * qa); gq[2] += gR[7] * (2.0 * qd); gq[3] += gR[7] * (2.0 * qc);
-        /* R22 = 1 - 2(b^2 + c^2) */
-        gq[1] += gR[8] * (-4.0 * qb); gq[2] += gR[8] * (-4.0 * qc);
-        /* q^ = q / |q| */
-        double qdot = qa * gq[0] + qb * gq[1] + qc * gq[2] + qd * gq[3];
-        for (int k = 0; k < 4; ++k) gout[3 + k] = (gq[k] - P.qn[k] * qdot) / P.qlen;
+        double ds;
+        chain_to_params(&P, &cam, h, hw, sigma, &sg, gout, &ds);
+        dsig_total += ds;
+        dsig_abs += fabs(ds);
     }
-    if (dsigma) { dsigma[0] = dsig_total; dsigma[1] = dsig_abs; }
+    if (dsigma) { dsigma[0] = dsig_total; dsigma[1] = dsig_abs; dsigma[2] = dsig_flip; }
     return 0;
 }
 

@@ -34,7 +34,7 @@ EXPORTED = (
     "sparseoit_commit_frozen", "sparseoit_get_frozen", "sparseoit_forward", "sparseoit_backward",
     "sparseoit_reserve_pairs", "sparseoit_status", "sparseoit_last_counts", "sparseoit_set_counting",
     "sparseoit_set_profiling", "sparseoit_get_profile", "sparseoit_last_error", "sparseoit_version",
-    "sparseoit_compact_active_static",
+    "sparseoit_compact_active_static", "sparseoit_autotune",
 )
 STATIC_MAX_SPLATS = 16 * 1024 * 1024
 
@@ -62,9 +62,15 @@ class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("fwd_pixels_per_thread", ctypes.c_int32), ("n_candidates", ctypes.c_int32),
+                ("candidates", ctypes.c_int32 * 4), ("ms", ctypes.c_float * 4)]
+
+
 class Config(ctypes.Structure):
     _fields_ = [("max_pairs", ctypes.c_int64), ("fwd_pixels_per_thread", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("proj_lanes_per_splat", ctypes.c_int32), ("bwd_group_by_cell", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 _lock = threading.Lock()
@@ -101,6 +107,8 @@ def load(path: str = LIB_PATH):
             "sparseoit_last_error": ([vp], ctypes.c_char_p),
             "sparseoit_version": ([], ctypes.c_int),
             "sparseoit_compact_active_static": ([vp, i64, vp, vp, vp], ctypes.c_int),
+            "sparseoit_autotune": ([vp, P(Splats), P(Camera), P(i32), i32, P(vp), P(vp), vp, i32, P(Tuning), vp],
+                                   ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)

@@ -23,6 +23,8 @@ struct sparseoit_ctx {
     std::vector<int> W, H;
     int64_t pair_cap = 0;
     int fwd_strip = 4;            // pixels per thread of the forward raster
+    int proj_lanes = 4;           // lanes per splat of the projection
+    bool bwd_group = false;       // backward: group a tile's splats by centre cell
     std::string err;
 
     // active set
@@ -191,8 +193,8 @@ static int render_pass_bin(sparseoit_ctx *ctx, Batch &b, const sparseoit_splats 
     const SplatPtrs sp = splat_ptrs(s);
     {
         ProfScope ps(ctx, "project", st);
-        launch_project(b, sp, s->sh_dtype == SPARSEOIT_BF16, list1, n1, list2, n2, ctx->d_rec, ctx->d_ext,
-                       ctx->d_tile_count, st);
+        launch_project(b, sp, s->sh_dtype == SPARSEOIT_BF16, ctx->proj_lanes, list1, n1, list2, n2, ctx->d_rec,
+                       ctx->d_ext, ctx->d_tile_count, st);
     }
     CK_LAUNCH("project_kernel");
     {
@@ -268,6 +270,15 @@ int sparseoit_create(sparseoit_ctx **out, int64_t max_splats, int32_t n_views, c
         }
         ctx->fwd_strip = s;
     }
+    if (cfg && cfg->proj_lanes_per_splat != 0) {
+        const int l = cfg->proj_lanes_per_splat;
+        if (l != 4 && l != 16) {
+            delete ctx;
+            return fail(nullptr, SPARSEOIT_ERR_INVALID_ARG, "proj_lanes_per_splat must be 4 or 16");
+        }
+        ctx->proj_lanes = l;
+    }
+    if (cfg && cfg->bwd_group_by_cell != 0) ctx->bwd_group = cfg->bwd_group_by_cell > 0;
     if (ctx->pair_cap > 0x7fffffffll) ctx->pair_cap = 0x7fffffffll;
     ctx->view_gen.assign(n_views, -1);
     ctx->d_frozen.assign(n_views, nullptr);
@@ -505,7 +516,8 @@ int sparseoit_backward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const
     CK(cudaMemsetAsync(ctx->d_sgrad, 0, (size_t)(3 * nrec) * sizeof(float4), st), "memset(screen grads)");
     {
         ProfScope ps(ctx, "raster_bwd", st);
-        launch_raster_bwd(b, ctx->d_rec, ctx->d_offsets, ctx->d_pairs, ctx->pair_cap, ctx->d_sgrad, st);
+        launch_raster_bwd(b, ctx->bwd_group, ctx->d_rec, ctx->d_offsets, ctx->d_pairs, ctx->pair_cap, ctx->d_sgrad,
+                          st);
     }
     CK_LAUNCH("raster_bwd_kernel");
     if (!out->accumulate) CK(cudaMemsetAsync(out->sigma, 0, sizeof(float), st), "memset(dsigma)");
@@ -519,6 +531,51 @@ int sparseoit_backward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const
     }
     CK_LAUNCH("project_bwd_kernel");
     return SPARSEOIT_OK;
+}
+
+int sparseoit_autotune(sparseoit_ctx *ctx, const sparseoit_splats *splats, const sparseoit_camera *cams,
+                       const int32_t *views, int32_t n_views, float *const *d_images, const float *const *d_targets,
+                       float *d_loss, int32_t reps, sparseoit_tuning *out, void *stream) {
+    if (!ctx || !out) return SPARSEOIT_ERR_INVALID_ARG;
+    if (reps < 1) reps = 3;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int cand[3] = {1, 2, 4};
+    memset(out, 0, sizeof(*out));
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a), "autotune event");
+    CK(cudaEventCreate(&b), "autotune event");
+    const bool prof = ctx->profiling;
+    ctx->profiling = false;
+    int best = ctx->fwd_strip;
+    float best_ms = 0.f;
+    int rc = SPARSEOIT_OK;
+    for (int c = 0; c < 3 && rc == SPARSEOIT_OK; ++c) {
+        ctx->fwd_strip = cand[c];
+        rc = sparseoit_forward(ctx, splats, cams, views, n_views, d_images, d_targets, d_loss, stream);
+        if (rc) break;
+        cudaEventRecord(a, st);
+        for (int r = 0; r < reps && rc == SPARSEOIT_OK; ++r)
+            rc = sparseoit_forward(ctx, splats, cams, views, n_views, d_images, d_targets, d_loss, stream);
+        cudaEventRecord(b, st);
+        if (rc) break;
+        cudaError_t e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e != cudaSuccess) { rc = cuda_check(ctx, e, "autotune timing"); break; }
+        ms /= (float)reps;
+        out->candidates[out->n_candidates] = cand[c];
+        out->ms[out->n_candidates] = ms;
+        out->n_candidates++;
+        if (c == 0 || ms < best_ms) { best_ms = ms; best = cand[c]; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->profiling = prof;
+    ctx->fwd_strip = best;
+    out->fwd_pixels_per_thread = best;
+    if (rc) return rc;
+    // leave valid outputs of the chosen configuration
+    return sparseoit_forward(ctx, splats, cams, views, n_views, d_images, d_targets, d_loss, stream);
 }
 
 int sparseoit_reserve_pairs(sparseoit_ctx *ctx, int64_t max_pairs) {

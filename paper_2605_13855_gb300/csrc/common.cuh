@@ -5,7 +5,7 @@
 //       rec[3q+0] = (mu'x, mu'y, r, A2)        quadratic form, see below
 //       rec[3q+1] = (B2, log2 o, w, yh)        yh = y half-extent of the cutoff ellipse
 //       rec[3q+2] = (c_r, c_g, c_b, sign)      sign = +1 / -1 (frozen-sum update)
-//     ext[q] = (tau2', y half-extent, x half-extent, dy of the x extreme)
+//     ext[q] = (tau2', y half-extent, 1 / A2, dy of the x extreme)
 //   * tile bins: one tile id space for all views of the batch (view v owns
 //     [tile_base, tile_base + tiles_x * tiles_y)); offsets[t] .. offsets[t+1]
 //     index the u32 pair arena that holds record indices q (no depth key).
@@ -148,6 +148,37 @@ __device__ __forceinline__ void sh_grad16(float x, float y, float z, const float
     gx += a[14] * 2.f * C3e * x * z;   gy -= a[14] * 2.f * C3e * y * z;  gz += a[14] * C3e * (xx - yy);
     gx += a[15] * 3.f * C3a * (xx - yy);   gy -= a[15] * 6.f * C3a * x * y;
     g[0] = gx; g[1] = gy; g[2] = gz;
+}
+
+// Cooperative SH evaluation by a group of G lanes (G = 4 or 16; lane k of the
+// group holds coefficients k, k + G, ...): the basis value of coefficient
+// k + G j for this lane, picked without dynamic register indexing.
+template <int G>
+__device__ __forceinline__ void sh_basis_group(float x, float y, float z, int k, float yk[16 / G]) {
+    float Y[16];
+    sh_basis16(x, y, z, Y);
+#pragma unroll
+    for (int j = 0; j < 16 / G; ++j) {
+        float v = Y[G * j];
+#pragma unroll
+        for (int m = 1; m < G; ++m) v = (k == m) ? Y[G * j + m] : v;
+        yk[j] = v;
+    }
+}
+
+// Mask of the G lanes of this lane's group (groups are aligned in the warp).
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+    return (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (threadIdx.x & 31 & ~(G - 1)));
+}
+
+// Sum of v over the G lanes of this lane's group (result in every lane); all
+// G lanes must call it together.
+template <int G>
+__device__ __forceinline__ float group_sum(float v, unsigned mask) {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) v += __shfl_xor_sync(mask, v, off);
+    return v;
 }
 
 // Rotation of the unit quaternion (w, x, y, z), row-major.

@@ -4,8 +4,9 @@
 
 namespace soit {
 
-int launch_project(const Batch &b, const SplatPtrs &sp, bool bf16, const int *list1, int n1, const int *list2, int n2,
-                   float4 *rec, float4 *ext, int *tile_count, cudaStream_t st);
+// lanes = lanes per splat of the projection (4 or 16).
+int launch_project(const Batch &b, const SplatPtrs &sp, bool bf16, int lanes, const int *list1, int n1,
+                   const int *list2, int n2, float4 *rec, float4 *ext, int *tile_count, cudaStream_t st);
 int launch_scan_tiles(const int *count, int total, int *offsets, int *cursor, int64_t cap, unsigned *status,
                       int64_t *pairs_out, cudaStream_t st);
 int launch_scatter(const Batch &b, const float4 *rec, const float4 *ext, int *cursor, uint32_t *pairs, int64_t cap,
@@ -18,8 +19,9 @@ int launch_raster_fwd(const Batch &b, int mode, int strip, const float4 *rec, co
                       cudaStream_t st);
 
 int launch_prep_state(const Batch &b, const float bg[3], cudaStream_t st);
-int launch_raster_bwd(const Batch &b, const float4 *rec, const int *offsets, const uint32_t *pairs, int64_t cap,
-                      float4 *sgrad, cudaStream_t st);
+// group: order each round of a tile's splats by centre cell before splitting it into warps.
+int launch_raster_bwd(const Batch &b, bool group, const float4 *rec, const int *offsets, const uint32_t *pairs,
+                      int64_t cap, float4 *sgrad, cudaStream_t st);
 
 struct GradPtrs {
     float *means, *quats, *log_scales, *opacity_logits, *sh_color, *sh_weight, *sigma;

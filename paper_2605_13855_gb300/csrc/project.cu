@@ -16,7 +16,7 @@ namespace soit {
 
 // Tiles of view vd met by the ellipse
 //     (A2 (dx - r dy))^2 + (B2 dy)^2 <= tau2,   (dx, dy) = pixel centre - (mx, my),
-// e = (tau2, y half-extent, x half-extent, dy at the rightmost point).
+// e = (tau2, y half-extent, 1 / A2, dy at the rightmost point).
 // tile_rows gives the tile rows [ty0, ty1]; row_tiles the tile columns
 // [tx0, tx1] of one tile row.  For the band of pixel-centre rows of a tile
 // row, the x-range of the ellipse is [mx + xl(dL), mx + xr(dR)] where
@@ -36,16 +36,25 @@ __device__ __forceinline__ bool tile_rows(const ViewDesc &vd, float my, const fl
     return true;
 }
 
-__device__ __forceinline__ bool row_tiles(const ViewDesc &vd, float mx, float my, float r, float A2, float B2,
+// Square root by the PTX approximate instruction: deterministic for a given
+// input, which is all the two passes need (the cutoff already carries a 2e-3
+// relative margin for its error).
+__device__ __forceinline__ float approx_sqrt(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ bool row_tiles(const ViewDesc &vd, float mx, float my, float r, float B2,
                                           const float4 e, int ty, int &tx0, int &tx1) {
-    const float tau2 = e.x, yh = e.y, dys = e.w;
+    const float tau2 = e.x, yh = e.y, invA2 = e.z, dys = e.w;
     const float ylo = fmaxf(__fsub_rn((float)(ty * kTile) + 0.5f, my), -yh);
     const float yhi = fminf(__fsub_rn((float)(ty * kTile + kTile - 1) + 0.5f, my), yh);
     if (ylo > yhi) return false;
-    const float invA2 = __fdiv_rn(1.f, A2), B2sq = __fmul_rn(B2, B2);
+    const float B2sq = __fmul_rn(B2, B2);
     const float dR = fminf(fmaxf(dys, ylo), yhi), dL = fminf(fmaxf(-dys, ylo), yhi);
-    const float hR = __fmul_rn(__fsqrt_rn(fmaxf(__fsub_rn(tau2, __fmul_rn(B2sq, __fmul_rn(dR, dR))), 0.f)), invA2);
-    const float hL = __fmul_rn(__fsqrt_rn(fmaxf(__fsub_rn(tau2, __fmul_rn(B2sq, __fmul_rn(dL, dL))), 0.f)), invA2);
+    const float hR = __fmul_rn(approx_sqrt(fmaxf(__fsub_rn(tau2, __fmul_rn(B2sq, __fmul_rn(dR, dR))), 0.f)), invA2);
+    const float hL = __fmul_rn(approx_sqrt(fmaxf(__fsub_rn(tau2, __fmul_rn(B2sq, __fmul_rn(dL, dL))), 0.f)), invA2);
     const float xr = __fadd_rn(mx, __fadd_rn(__fmul_rn(r, dR), hR));
     const float xl = __fadd_rn(mx, __fsub_rn(__fmul_rn(r, dL), hL));
     const int px0 = f2i_clamped(ceilf(__fsub_rn(xl, 0.501f)), 0, vd.W);
@@ -56,37 +65,53 @@ __device__ __forceinline__ bool row_tiles(const ViewDesc &vd, float mx, float my
     return true;
 }
 
-// One thread per list entry r; loops over the views of the batch so that the
-// splat's parameters are read from HBM once.  List entry r < n1 is splat
-// list1[r] with sign +1, r >= n1 is splat list2[r - n1] with sign -1.
-template <typename ShT>
+// G lanes (G = 4 or 16) per list entry r, looping over the views of the
+// batch so that the splat's parameters are read from HBM once.  Lane k of the
+// group loads SH coefficients k, k + G, ... (a coalesced row per splat), the
+// lanes evaluate their basis values and sum the products with shuffles; the
+// geometry is evaluated redundantly by the G lanes; the tile rows of the
+// cutoff ellipse are counted by the lanes in parallel.  List entry r < n1 is
+// splat list1[r] with sign +1, r >= n1 is splat list2[r - n1] with sign -1.
+template <typename ShT, int G>
 __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Batch b, SplatPtrs sp,
                                                       const int *__restrict__ list1, int n1,
                                                       const int *__restrict__ list2, int n2, float4 *__restrict__ rec,
                                                       float4 *__restrict__ ext, int *__restrict__ tile_count) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int J = 16 / G;
+    const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G);  // uniform in a group
+    const int k = threadIdx.x & (G - 1);
     const int n_list = n1 + n2;
-    if (r >= n_list) return;
+    if (r >= n_list) return;  // whole groups leave together
     const int i = r < n1 ? list1[r] : list2[r - n1];
     const float sign = r < n1 ? 1.f : -1.f;
 
     float mu[3], q[4], ls[3];
-    for (int k = 0; k < 3; ++k) mu[k] = __ldg(sp.means + 3 * (int64_t)i + k);
+    for (int j = 0; j < 3; ++j) mu[j] = __ldg(sp.means + 3 * (int64_t)i + j);
     const float4 q4 = __ldg(reinterpret_cast<const float4 *>(sp.quats) + i);
     q[0] = q4.x; q[1] = q4.y; q[2] = q4.z; q[3] = q4.w;
-    for (int k = 0; k < 3; ++k) ls[k] = __ldg(sp.log_scales + 3 * (int64_t)i + k);
+    for (int j = 0; j < 3; ++j) ls[j] = __ldg(sp.log_scales + 3 * (int64_t)i + j);
     const float ol = __ldg(sp.opacity_logits + i);
     const float o = 1.f / (1.f + expf(-ol));
     const float log2o = log2f(o);
     const ShT *hc = reinterpret_cast<const ShT *>(sp.sh_color) + 48 * (int64_t)i;
     const ShT *hw = reinterpret_cast<const ShT *>(sp.sh_weight) + 16 * (int64_t)i;
+    float h0[J], h1[J], h2[J], hv[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int kk = k + G * j;
+        h0[j] = ldf(hc, 3 * kk + 0);
+        h1[j] = ldf(hc, 3 * kk + 1);
+        h2[j] = ldf(hc, 3 * kk + 2);
+        hv[j] = ldf(hw, kk);
+    }
 
     for (int v = 0; v < b.n_views; ++v) {
         const ViewDesc &vd = b.v[v];
         const int64_t qidx = (int64_t)v * n_list + r;
-        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = make_float4(0.f, -INFINITY, 0.f, 0.f);
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = make_float4(0.f, -INFINITY, 0.f, -1.f);
         float4 r2 = make_float4(0.f, 0.f, 0.f, sign), e = make_float4(-1.f, 0.f, 0.f, 0.f);
         SplatGeom g;
+        // the culling decision is uniform over the half-warp (same inputs, same code)
         if (o >= (1.f / 255.f) && splat_geometry(vd, mu, q, ls, g)) {
             const float z = g.tc[2], iz = 1.f / z;
             const float mx = fmaf(vd.fx, g.tc[0] * iz, vd.cx), my = fmaf(vd.fy, g.tc[1] * iz, vd.cy);
@@ -95,16 +120,19 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Ba
             const float B2 = sqrtf(kLog2e / (2.f * g.syy));
             // Eq. 4: SH colour and (Eq. 1) the single-channel weight SH
             const float idl = 1.f / g.dlen;
-            float Y[16];
-            sh_basis16(g.d[0] * idl, g.d[1] * idl, g.d[2] * idl, Y);
-            float c0 = 0.5f, c1 = 0.5f, c2 = 0.5f, vv = 0.5f;
+            float yk[J];
+            sh_basis_group<G>(g.d[0] * idl, g.d[1] * idl, g.d[2] * idl, k, yk);
+            float p0 = 0.f, p1 = 0.f, p2 = 0.f, pv = 0.f;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                c0 = fmaf(Y[k], ldf(hc, 3 * k + 0), c0);
-                c1 = fmaf(Y[k], ldf(hc, 3 * k + 1), c1);
-                c2 = fmaf(Y[k], ldf(hc, 3 * k + 2), c2);
-                vv = fmaf(Y[k], ldf(hw, k), vv);
+            for (int j = 0; j < J; ++j) {
+                p0 = fmaf(yk[j], h0[j], p0);
+                p1 = fmaf(yk[j], h1[j], p1);
+                p2 = fmaf(yk[j], h2[j], p2);
+                pv = fmaf(yk[j], hv[j], pv);
             }
+            const unsigned gm = group_mask<G>();
+            const float c0 = group_sum<G>(p0, gm) + 0.5f, c1 = group_sum<G>(p1, gm) + 0.5f;
+            const float c2 = group_sum<G>(p2, gm) + 0.5f, vv = group_sum<G>(pv, gm) + 0.5f;
             const float w = fmaxf(0.f, 1.f - z / sp.sigma) * fmaxf(vv, 0.f);
             // cutoff: log2 alpha_raw >= -log2 255  <=>  quadratic <= log2(255 o);
             // widened slightly so that binning is a strict superset of the
@@ -119,22 +147,22 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Ba
                 r0 = make_float4(mx, my, rr, A2);
                 r1 = make_float4(B2, log2o, w, yh);
                 r2 = make_float4(fmaxf(c0, 0.f), fmaxf(c1, 0.f), fmaxf(c2, 0.f), sign);
-                e = make_float4(tau2, yh, xh, dys);
+                e = make_float4(tau2, yh, 1.f / A2, dys);
                 int ty0, ty1;
                 if (tile_rows(vd, my, e, ty0, ty1)) {
-                    for (int ty = ty0; ty <= ty1; ++ty) {
+                    for (int ty = ty0 + k; ty <= ty1; ty += G) {
                         int tx0, tx1;
-                        if (!row_tiles(vd, mx, my, rr, A2, B2, e, ty, tx0, tx1)) continue;
+                        if (!row_tiles(vd, mx, my, rr, B2, e, ty, tx0, tx1)) continue;
                         int *row = tile_count + vd.tile_base + ty * vd.tiles_x;
                         for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(row + tx, 1);
                     }
                 }
             }
         }
-        rec[3 * qidx + 0] = r0;
-        rec[3 * qidx + 1] = r1;
-        rec[3 * qidx + 2] = r2;
-        ext[qidx] = e;
+        if (k == 0) rec[3 * qidx + 0] = r0;
+        else if (k == 1) rec[3 * qidx + 1] = r1;
+        else if (k == 2) rec[3 * qidx + 2] = r2;
+        else if (k == 3) ext[qidx] = e;
     }
 }
 
@@ -198,15 +226,18 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(const int *__restrict_
     }
 }
 
-// One warp per list entry: the warp walks the entry's tile rows and its
-// lanes take the columns of a row in parallel, so the position-returning
-// atomics of a splat overlap instead of running one after another.
-__global__ void __launch_bounds__(256) scatter_kernel(const __grid_constant__ Batch b, const float4 *__restrict__ rec,
-                                                      const float4 *__restrict__ ext, int *__restrict__ cursor,
-                                                      uint32_t *__restrict__ pairs, int64_t cap) {
+// One warp per list entry.  Lanes compute the column range of one tile row
+// each (32 rows at a time), a warp scan of the per-row counts flattens the
+// entry's tile list, and each lane then takes one (row, column) of it, so a
+// typical splat costs one round of position-returning atomics instead of one
+// per row.
+__global__ void __launch_bounds__(256, 4) scatter_kernel(const __grid_constant__ Batch b,
+                                                         const float4 *__restrict__ rec,
+                                                         const float4 *__restrict__ ext, int *__restrict__ cursor,
+                                                         uint32_t *__restrict__ pairs, int64_t cap) {
     const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (r >= b.n_list) return;
+    if (r >= b.n_list) return;  // whole warps leave together
     for (int v = 0; v < b.n_views; ++v) {
         const ViewDesc &vd = b.v[v];
         const int64_t qidx = (int64_t)v * b.n_list + r;
@@ -216,27 +247,61 @@ __global__ void __launch_bounds__(256) scatter_kernel(const __grid_constant__ Ba
         const float4 r0 = rec[3 * qidx + 0];
         if (!tile_rows(vd, r0.y, e, ty0, ty1)) continue;
         const float B2 = rec[3 * qidx + 1].x;
-        for (int ty = ty0; ty <= ty1; ++ty) {
-            int tx0, tx1;
-            if (!row_tiles(vd, r0.x, r0.y, r0.z, r0.w, B2, e, ty, tx0, tx1)) continue;
-            int *row = cursor + vd.tile_base + ty * vd.tiles_x;
-            for (int tx = tx0 + lane; tx <= tx1; tx += 32) {
-                const int pos = atomicAdd(row + tx, 1);
-                if ((int64_t)pos < cap) pairs[pos] = (uint32_t)qidx;
+        for (int tyb = ty0; tyb <= ty1; tyb += 32) {
+            const int ty = tyb + lane;
+            int tx0 = 0, cnt = 0;
+            if (ty <= ty1) {
+                int a0, a1;
+                if (row_tiles(vd, r0.x, r0.y, r0.z, B2, e, ty, a0, a1)) {
+                    tx0 = a0;
+                    cnt = a1 - a0 + 1;
+                }
+            }
+            int incl = cnt;  // inclusive scan of the per-row tile counts
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int base = 0; base < total; base += 32) {
+                const int idx = base + lane;
+                // row of flattened entry idx: the number of rows whose inclusive count is <= idx
+                int row = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int probe = __shfl_sync(0xffffffffu, incl, row + step - 1);
+                    if (probe <= idx) row += step;
+                }
+                const int row_tx0 = __shfl_sync(0xffffffffu, tx0, row & 31);
+                const int row_excl = __shfl_sync(0xffffffffu, incl - cnt, row & 31);
+                if (idx < total) {
+                    const int t = vd.tile_base + (tyb + row) * vd.tiles_x + row_tx0 + (idx - row_excl);
+                    const int pos = atomicAdd(cursor + t, 1);
+                    if ((int64_t)pos < cap) pairs[pos] = (uint32_t)qidx;
+                }
             }
         }
     }
 }
 
-int launch_project(const Batch &b, const SplatPtrs &sp, bool bf16, const int *list1, int n1, const int *list2, int n2,
-                   float4 *rec, float4 *ext, int *tile_count, cudaStream_t st) {
-    const int n = n1 + n2;
-    if (n == 0) return 0;
-    const int grid = (n + 255) / 256;
+template <int G>
+static void launch_project_g(const Batch &b, const SplatPtrs &sp, bool bf16, const int *list1, int n1,
+                             const int *list2, int n2, float4 *rec, float4 *ext, int *tile_count, cudaStream_t st) {
+    const int grid = (int)(((int64_t)(n1 + n2) * G + 255) / 256);
     if (bf16)
-        project_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(b, sp, list1, n1, list2, n2, rec, ext, tile_count);
+        project_kernel<__nv_bfloat16, G><<<grid, 256, 0, st>>>(b, sp, list1, n1, list2, n2, rec, ext, tile_count);
     else
-        project_kernel<float><<<grid, 256, 0, st>>>(b, sp, list1, n1, list2, n2, rec, ext, tile_count);
+        project_kernel<float, G><<<grid, 256, 0, st>>>(b, sp, list1, n1, list2, n2, rec, ext, tile_count);
+}
+
+int launch_project(const Batch &b, const SplatPtrs &sp, bool bf16, int lanes, const int *list1, int n1,
+                   const int *list2, int n2, float4 *rec, float4 *ext, int *tile_count, cudaStream_t st) {
+    if (n1 + n2 == 0) return 0;
+    if (lanes == 16)
+        launch_project_g<16>(b, sp, bf16, list1, n1, list2, n2, rec, ext, tile_count, st);
+    else
+        launch_project_g<4>(b, sp, bf16, list1, n1, list2, n2, rec, ext, tile_count, st);
     return 0;
 }
 

@@ -30,6 +30,11 @@ namespace soit {
 // (the dy sums taken per tile row, where dy is constant) gives
 //   dL/dmu'x = -K A2 Se,  dL/dmu'y = K (A2 r Se - B2^2 Sdy),
 //   dL/dr = -K A2 Sey,    dL/dA2 = K See / A2,  dL/dB2 = K B2 Sdyy.
+// kGroup: before a round of 256 of the tile's splats is split into warps, a
+// shared-memory counting sort orders it by the 4x4-pixel cell of the tile
+// that holds the splat's centre (clamped), so that the 32 splats of a warp
+// tend to cover the same pixels and fewer lanes idle in the per-pixel work.
+template <bool kGroup>
 __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(const __grid_constant__ Batch b,
                                                               const float4 *__restrict__ rec,
                                                               const int *__restrict__ offsets,
@@ -37,6 +42,8 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(const __grid_const
                                                               uint32_t nrec, float4 *__restrict__ sgrad) {
     __shared__ float4 sa[kTilePix];  // g0, g1, g2, A
     __shared__ float2 sb[kTilePix];  // B, gF
+    __shared__ uint32_t sorted[kGroup ? kTilePix : 1];
+    __shared__ int hist[17];
 
     const int gt = blockIdx.x;
     const int v = find_view(b, gt);
@@ -64,9 +71,45 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(const __grid_const
     const int warp = tid >> 5, lane = tid & 31;
     const float ox = (float)(tx * kTile) + 0.5f, oy = (float)(ty * kTile) + 0.5f;
 
-    for (int cb = start + warp * 32; cb < end; cb += kTilePix) {
-        const int idx = cb + lane;
-        const uint32_t q = idx < end ? pairs[idx] : 0xffffffffu;
+    for (int cb0 = start; cb0 < end; cb0 += kTilePix) {
+        uint32_t q;
+        if (kGroup) {
+            const int nr = min(kTilePix, end - cb0);
+            uint32_t myq = 0xffffffffu;
+            int cell = 16, slot = 0;
+            if (tid < 16) hist[tid] = 0;
+            __syncthreads();
+            if (tid < nr) {
+                myq = pairs[cb0 + tid];
+                cell = 15;
+                if (myq < nrec) {
+                    const float4 c0r = rec[3 * (int64_t)myq + 0];
+                    const int cx = f2i_clamped(floorf((c0r.x - (ox - 0.5f)) * 0.25f), 0, 3);
+                    const int cy = f2i_clamped(floorf((c0r.y - (oy - 0.5f)) * 0.25f), 0, 3);
+                    cell = cy * 4 + cx;
+                }
+                slot = atomicAdd(&hist[cell], 1);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                int run = 0;
+                for (int c = 0; c < 16; ++c) {
+                    const int t = hist[c];
+                    hist[c] = run;
+                    run += t;
+                }
+            }
+            __syncthreads();
+            if (tid < nr) sorted[hist[cell] + slot] = myq;
+            __syncthreads();
+            const int idx = warp * 32 + lane;
+            q = idx < nr ? sorted[idx] : 0xffffffffu;
+            if (cb0 + warp * 32 >= end) continue;  // this warp has no splat in this round
+        } else {
+            const int idx = cb0 + warp * 32 + lane;
+            if (cb0 + warp * 32 >= end) continue;
+            q = idx < end ? pairs[idx] : 0xffffffffu;
+        }
         const bool valid = q < nrec;
         float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = make_float4(0.f, -INFINITY, 0.f, -1.f), a2 = a0;
         if (valid) {
@@ -164,11 +207,14 @@ int launch_prep_state(const Batch &b, const float bg[3], cudaStream_t st) {
     return 0;
 }
 
-int launch_raster_bwd(const Batch &b, const float4 *rec, const int *offsets, const uint32_t *pairs, int64_t cap,
-                      float4 *sgrad, cudaStream_t st) {
+int launch_raster_bwd(const Batch &b, bool group, const float4 *rec, const int *offsets, const uint32_t *pairs,
+                      int64_t cap, float4 *sgrad, cudaStream_t st) {
     if (b.total_tiles == 0) return 0;
     const uint32_t nrec = (uint32_t)((int64_t)b.n_views * b.n_list);
-    raster_bwd_kernel<<<b.total_tiles, kTilePix, 0, st>>>(b, rec, offsets, pairs, cap, nrec, sgrad);
+    if (group)
+        raster_bwd_kernel<true><<<b.total_tiles, kTilePix, 0, st>>>(b, rec, offsets, pairs, cap, nrec, sgrad);
+    else
+        raster_bwd_kernel<false><<<b.total_tiles, kTilePix, 0, st>>>(b, rec, offsets, pairs, cap, nrec, sgrad);
     return 0;
 }
 

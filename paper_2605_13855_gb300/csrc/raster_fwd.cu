@@ -6,8 +6,9 @@
 // splats whose cutoff ellipse misses those rows.  The tile's records are staged through shared
 // memory 256 at a time, already shifted to tile-relative offsets.  Every
 // pixel accumulates over the tile's splats P += a w c, Q += a w and
-// T *= (1 - a), with per-batch partial sums for P and Q to hold the FP32
-// rounding of long sums.  The epilogue depends on the mode:
+// T *= (1 - a) (log T += log(1 - a) for the frozen sums), the sums taken in
+// 32-splat blocks added to the total, so that the FP32 rounding of sums over
+// thousands of splats stays at the level of about 32 + n/32 additions.  The epilogue depends on the mode:
 //   kRasterFused: combine with the view's frozen sums (P_F, Q_F, log T_F),
 //     write C = T c0 + (1 - T) P/Q, the L1 loss and the backward pixel state
 //     (g, A = T g.(F - c0), B = (1 - T)/Q, g.F) with g = sign(C - I)/(3HW).
@@ -83,10 +84,13 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
             if (kMode == kRasterSums) ssign[k] = q < nrec ? rec[3 * (int64_t)q + 2].w : 0.f;
         }
         __syncthreads();
-        float b0[kStrip], b1[kStrip], b2[kStrip], bq[kStrip];
+        // two-level summation: 32-splat blocks into the total
+        for (int jb = 0; jb < n; jb += 32) {
+        float b0[kStrip], b1[kStrip], b2[kStrip], bq[kStrip], bl[kStrip];
 #pragma unroll
-        for (int j = 0; j < kStrip; ++j) b0[j] = b1[j] = b2[j] = bq[j] = 0.f;
-        for (int j = 0; j < n; ++j) {
+        for (int j = 0; j < kStrip; ++j) b0[j] = b1[j] = b2[j] = bq[j] = bl[j] = 0.f;
+        const int je = min(n, jb + 32);
+        for (int j = jb; j < je; ++j) {
             const float4 a0 = s0[j], a1 = s1[j];
             // warp-uniform: the ellipse misses this warp's rows
             const float dlo = a0.y + (float)wrow;
@@ -104,7 +108,7 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
                     b2[p] = fmaf(a, a2.z, b2[p]);
                     bq[p] = fmaf(a, a2.w, bq[p]);
                     if (kMode == kRasterSums)
-                        T[p] = fmaf(ssign[j], log1pf(-a), T[p]);
+                        bl[p] = fmaf(ssign[j], log1pf(-a), bl[p]);
                     else
                         T[p] = fmaf(-T[p], a, T[p]);
                     if (kCount) n_contrib += (tx * kTile + sx + p < vd.W && ty * kTile + ky < vd.H) ? 1u : 0u;
@@ -117,6 +121,8 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
             P1[p] += b1[p];
             P2[p] += b2[p];
             Q[p] += bq[p];
+            if (kMode == kRasterSums) T[p] += bl[p];
+        }
         }
     }
 

@@ -112,7 +112,7 @@ class Renderer:
     """A SparseOIT context: active set, per-view frozen sums, batched fwd / bwd."""
 
     def __init__(self, n_splats: int, view_sizes: Sequence[Sequence[int]], max_pairs: int = 0,
-                 fwd_pixels_per_thread: int = 0):
+                 fwd_pixels_per_thread: int = 0, proj_lanes_per_splat: int = 0, bwd_group_by_cell: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("sparseoit needs a CUDA device")
         self.lib = _lib.load()
@@ -124,6 +124,8 @@ class Renderer:
         cfg = _lib.Config()
         cfg.max_pairs = int(max_pairs)
         cfg.fwd_pixels_per_thread = int(fwd_pixels_per_thread)
+        cfg.proj_lanes_per_splat = int(proj_lanes_per_splat)
+        cfg.bwd_group_by_cell = int(bwd_group_by_cell)
         self._ctx = ctypes.c_void_p()
         rc = self.lib.sparseoit_create(ctypes.byref(self._ctx), self.n, nv, ws, hs, ctypes.byref(cfg))
         if rc != _lib.OK:
@@ -247,6 +249,30 @@ class Renderer:
         self._check(self.lib.sparseoit_backward(self._ctx, ctypes.byref(s), gptr, ctypes.byref(g),
                                                 ctypes.c_void_p(_stream_ptr(stream))))
         return out
+
+    def autotune(self, splats: SplatParams, cams: Sequence[dict], views: Sequence[int],
+                 targets: Optional[Sequence[torch.Tensor]] = None, reps: int = 3, stream=None):
+        """Pick the forward raster's pixels-per-thread for this batch (sparseoit_autotune).
+
+        Returns {"fwd_pixels_per_thread": chosen, "ms": {candidate: mean forward ms}}."""
+        nv = len(views)
+        s = splats_struct(splats)
+        camarr = (_lib.Camera * nv)(*[camera_struct(c) for c in cams])
+        varr = (ctypes.c_int32 * nv)(*[int(v) for v in views])
+        images = [torch.empty((self.view_sizes[v][1], self.view_sizes[v][0], 3), dtype=torch.float32, device="cuda")
+                  for v in views]
+        iptr = (ctypes.c_void_p * nv)(*[im.data_ptr() for im in images])
+        tptr, loss = None, None
+        if targets is not None:
+            tptr = (ctypes.c_void_p * nv)(*[tg.data_ptr() for tg in targets])
+            loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        t = _lib.Tuning()
+        self._check(self.lib.sparseoit_autotune(self._ctx, ctypes.byref(s), camarr, varr, nv, iptr, tptr,
+                                                ctypes.c_void_p(loss.data_ptr() if loss is not None else 0),
+                                                int(reps), ctypes.byref(t), ctypes.c_void_p(_stream_ptr(stream))))
+        self.forward_id += 1
+        return {"fwd_pixels_per_thread": int(t.fwd_pixels_per_thread),
+                "ms": {int(t.candidates[k]): float(t.ms[k]) for k in range(t.n_candidates)}}
 
     # ------------------------------------------------------------ misc
     def status(self, stream=None):

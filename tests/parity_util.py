@@ -1,25 +1,31 @@
 """Comparison helpers for the GPU-vs-oracle parity tests.
 
 Tolerances (stated for the FP32 CUDA path against the FP64 oracle):
-  * image: max |C_gpu - C_ref| / max |C_ref| <= 1e-5 over the pixels of a
-    view, excluding pixels where some splat's unclamped alpha lies within a
-    relative AMB_BAND of the 1/255 cut (there FP32 and FP64 may disagree on
-    whether the splat contributes at all; AMB_BAND = 1e-4 covers the FP32
-    error of the exponent at the cutoff edge of a small splat, ~6e-5 px of
-    centre rounding over a 2 px sigma; such pixels must stay below
-    AMB_PIX_MAX of the view);
-  * gradients: per parameter group, max |g_gpu - g_ref| / max |g_ref|
-    <= 1e-4, excluding splats with a pair within AMB_BAND of the 1/255 cut or
-    the 0.99 clamp, or a kink of max(0, .) (colour, weight, 1 - z/sigma)
-    within AMB_BAND.
+  * image: every pixel satisfies |C_gpu - C_ref| <= 1e-5 max|C_ref| + flip,
+    in every channel, where flip is the oracle's first-order bound on how far
+    the pairs whose unclamped alpha lies within a relative AMB_BAND of the
+    1/255 cut could move that pixel if included or dropped (FP32 and FP64
+    may decide those pairs differently).  AMB_BAND = 3e-4 covers the FP32
+    error of the exponent at the cutoff edge of a small splat far from the
+    principal point: ~1e-4 px of rounding in its projected centre over a
+    2 px sigma.
+  * gradients: per parameter group, every element satisfies
+    |g_gpu - g_ref| <= 1e-4 max|g_ref| + flip, flip being the sum over that
+    splat's pairs within AMB_BAND of the 1/255 cut or the 0.99 clamp of
+    |that pair's own gradient|; splats with a max(0, .) kink (colour,
+    weight, 1 - z/sigma) or the near plane within AMB_BAND are excluded (and
+    counted).  dL/dsigma (a sum whose terms cancel) is measured against the
+    sum of |per-splat terms|, plus its flip allowance.
 """
 import numpy as np
 import torch
 
+import oracle
+
 IMG_TOL = 1e-5
 GRAD_TOL = 1e-4
-AMB_BAND = 1e-4
-AMB_PIX_MAX = 1e-2
+AMB_BAND = 3e-4
+AMB_PIX_MAX = 0.05  # cap on the fraction of pixels whose allowance exceeds the tolerance itself
 
 GROUPS = dict(means=(0, 3), quats=(3, 7), log_scales=(7, 10), opacity_logits=(10, 11), sh_color=(11, 59),
               sh_weight=(59, 75))
@@ -29,34 +35,59 @@ def to_np(t):
     return t.detach().float().cpu().numpy().astype(np.float64)
 
 
-def image_error(img_gpu, ref_img, amb=None):
+def image_error(img_gpu, ref_img, flip=None):
+    """(max over pixels of (|C_gpu - C_ref| - flip)^+ / max|C_ref|, fraction of pixels whose
+    allowance flip exceeds IMG_TOL max|C_ref|, i.e. where the check is looser than the tolerance)."""
     a = to_np(img_gpu) if isinstance(img_gpu, torch.Tensor) else img_gpu
-    keep = np.ones(a.shape[:2], bool) if amb is None else (amb == 0)
     scale = max(np.abs(ref_img).max(), 1e-30)
-    return float(np.abs(a - ref_img)[keep].max(initial=0.0) / scale), float(1.0 - keep.mean())
+    d = np.abs(a - ref_img).max(axis=2)
+    frac = 0.0
+    if flip is not None:
+        d = np.maximum(d - flip, 0.0)
+        frac = float((flip > IMG_TOL * scale).mean())
+    return float(d.max(initial=0.0) / scale), frac
 
 
-def grad_errors(gpu: dict, ref: np.ndarray, rows: np.ndarray, keep: np.ndarray):
-    """gpu: dict of group -> array [len(rows), ...] in the order of `rows`;
-    ref: oracle grads [N, 75]; keep: bool over rows."""
+def oracle_grads(scene, cam, sums, dL_dC, active=None, window=None):
+    return oracle.backward_full(scene, cam, sums, dL_dC, active=active, window=window, amb_band=AMB_BAND,
+                                want_flip=True)
+
+
+def grad_errors(gpu: dict, ref, rows: np.ndarray, keep: np.ndarray, flip=None):
+    """Per group: max over kept rows of (|g_gpu - g_ref| - flip)^+ / max|g_ref|.
+    gpu: dict group -> array [len(rows), ...] in the order of `rows`; ref: [N, 75]."""
     out = {}
     for name, (lo, hi) in GROUPS.items():
         g = to_np(gpu[name]).reshape(len(rows), -1)[keep]
         r = ref[rows][keep, lo:hi]
+        d = np.abs(g - r)
+        if flip is not None:
+            d = np.maximum(d - flip[rows][keep, lo:hi], 0.0)
         scale = max(np.abs(r).max(initial=0.0), 1e-30)
-        out[name] = float(np.abs(g - r).max(initial=0.0) / scale)
+        out[name] = float(d.max(initial=0.0) / scale)
     return out
 
 
-def assert_grads_close(gpu, ref, rows, keep, tol=GRAD_TOL, dsig=None, dsig_ref=None, dsig_scale=None):
-    """Per-group normwise check; dL/dsigma (a sum over splats whose terms
-    cancel) is measured against the sum of the absolute terms."""
-    errs = grad_errors(gpu, ref, rows, keep)
+def assert_grads_close(gpu, ref, rows, keep, tol=GRAD_TOL, dsig=None, dsig_ref=None, dsig_scale=None, flip=None,
+                       dsig_flip=0.0):
+    errs = grad_errors(gpu, ref, rows, keep, flip)
     bad = {k: v for k, v in errs.items() if not v <= tol}
     assert not bad, f"gradient parity failed: {errs}"
     if dsig is not None:
         scale = dsig_scale if dsig_scale is not None else abs(dsig_ref)
-        rel = abs(dsig - dsig_ref) / max(scale, 1e-30)
+        rel = max(abs(dsig - dsig_ref) - dsig_flip, 0.0) / max(scale, 1e-30)
         errs["sigma"] = rel
         assert rel <= tol, f"dsigma {dsig} vs {dsig_ref} (rel {rel:.3g} of {scale:.3g})"
     return errs
+
+
+def check_against_oracle(grads_gpu, ref: dict, rows, min_keep=0.95):
+    """Gradient parity against an oracle.backward_full result (with flip); returns (errs, excluded fraction)."""
+    keep = (ref["amb"][rows] & 2) == 0
+    assert keep.mean() >= min_keep, f"too many kink-excluded splats: {1 - keep.mean():.3g}"
+    dsg = grads_gpu.get("sigma")
+    errs = assert_grads_close(grads_gpu, ref["grads"], rows, keep,
+                              dsig=None if dsg is None else float(dsg.reshape(-1)[0].item()),
+                              dsig_ref=ref["dsigma"], dsig_scale=ref["dsigma_scale"], flip=ref["flip"],
+                              dsig_flip=ref["dsigma_flip"])
+    return errs, float(1.0 - keep.mean())

@@ -62,8 +62,10 @@ int main(void) {
   F(sparseoit_splats, sh_color) F(sparseoit_splats, sh_dtype) F(sparseoit_splats, sigma) F(sparseoit_splats, bg)
   F(sparseoit_splats, n)
   F(sparseoit_grads, sigma) F(sparseoit_grads, rows_by_splat) F(sparseoit_grads, accumulate)
-  F(sparseoit_config, max_pairs) F(sparseoit_config, fwd_pixels_per_thread) F(sparseoit_config, reserved)
+  F(sparseoit_config, max_pairs) F(sparseoit_config, fwd_pixels_per_thread)
+  F(sparseoit_config, proj_lanes_per_splat) F(sparseoit_config, bwd_group_by_cell) F(sparseoit_config, reserved)
   F(sparseoit_kernel_time, launches) F(sparseoit_kernel_time, total_ms)
+  F(sparseoit_tuning, n_candidates) F(sparseoit_tuning, candidates) F(sparseoit_tuning, ms)
   return 0;
 }
 """
@@ -83,7 +85,8 @@ def test_ctypes_structs_match_header(tmp_path):
     assert got["config"] == ctypes.sizeof(_lib.Config)
     assert got["ktime"] == ctypes.sizeof(_lib.KernelTime)
     pairs = {"sparseoit_camera": _lib.Camera, "sparseoit_splats": _lib.Splats, "sparseoit_grads": _lib.Grads,
-             "sparseoit_config": _lib.Config, "sparseoit_kernel_time": _lib.KernelTime}
+             "sparseoit_config": _lib.Config, "sparseoit_kernel_time": _lib.KernelTime,
+             "sparseoit_tuning": _lib.Tuning}
     for key, off in got.items():
         if "." not in key:
             continue

@@ -7,7 +7,8 @@ import oracle
 from paper_2605_13855_gb300 import scenes
 from paper_2605_13855_gb300._lib import ERR_CAPACITY, ERR_STATE, SparseOITError
 from paper_2605_13855_gb300.renderer import Renderer, SparseOITRender, SplatParams
-from tests.parity_util import AMB_BAND, AMB_PIX_MAX, GRAD_TOL, IMG_TOL, assert_grads_close, image_error, to_np
+from tests.parity_util import AMB_BAND, AMB_PIX_MAX, GRAD_TOL, IMG_TOL, check_against_oracle, image_error, \
+    oracle_grads, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -41,23 +42,19 @@ def _check_view(r, sp, scene, cam, view, mask, seed, check_grads=True, window=No
     img = to_np(images[0])
     if window is not None:
         x0, y0, x1, y1 = window
-        e, frac = image_error(img[y0:y1, x0:x1], ref["image"][y0:y1, x0:x1], ref["amb"][y0:y1, x0:x1])
+        e, frac = image_error(img[y0:y1, x0:x1], ref["image"][y0:y1, x0:x1], ref["flip"][y0:y1, x0:x1])
     else:
-        e, frac = image_error(img, ref["image"], ref["amb"])
+        e, frac = image_error(img, ref["image"], ref["flip"])
     assert e <= IMG_TOL, f"image rel err {e:.3g}"
     assert frac <= AMB_PIX_MAX, f"ambiguous pixel fraction {frac:.3g}"
     if not check_grads:
         return e, None
     act = mask.astype(bool)
-    gref, dsig_ref, amb, dsig_scale = oracle.backward(scene, cam, ref["sums"], g, active=act, window=window,
-                                                      amb_band=AMB_BAND, with_scale=True)
+    ref_g = oracle_grads(scene, cam, ref["sums"], g, active=act, window=window)
     rows = np.where(act)[0]
-    keep = amb[rows] == 0
-    assert keep.mean() > 0.95, f"too many ambiguous splats: {1 - keep.mean():.3g}"
-    errs = assert_grads_close(grads, gref, rows, keep, dsig=float(grads["sigma"].item()), dsig_ref=dsig_ref,
-                              dsig_scale=dsig_scale)
-    print(f"parity {cam['width']}x{cam['height']}: image {e:.2e} (ambiguous px {frac:.2e}), grads",
-          {k: f"{v:.2e}" for k, v in errs.items()}, f"ambiguous splats {1 - keep.mean():.2e}")
+    errs, excl = check_against_oracle(grads, ref_g, rows)
+    print(f"parity {cam['width']}x{cam['height']}: image {e:.2e} (px with allowance > tol {frac:.2e}), grads",
+          {k: f"{v:.2e}" for k, v in errs.items()}, f"kink-excluded splats {excl:.2e}")
     return e, errs
 
 
@@ -94,10 +91,8 @@ def test_tiny_fused_l1():
     lref = np.abs(diff).mean()
     assert abs(loss.item() - lref) <= 1e-5 * lref
     g = np.sign(diff) / (3 * HW)
-    gref, dsig_ref, amb, dsig_scale = oracle.backward(scene, cam, ref["sums"], g, amb_band=AMB_BAND, with_scale=True)
-    rows = np.arange(n)
-    assert_grads_close(grads, gref, rows, amb == 0, dsig=float(grads["sigma"].item()), dsig_ref=dsig_ref,
-                       dsig_scale=dsig_scale)
+    ref_g = oracle_grads(scene, cam, ref["sums"], g)
+    check_against_oracle(grads, ref_g, np.arange(n))
 
 
 @pytest.mark.parametrize("frac", [0.0, 0.1, 1.0])
@@ -112,7 +107,7 @@ def test_active_set_equals_full_render(frac):
     if mask.sum() == 0:
         images, _ = r.forward(sp, [cam], [0])
         ref = oracle.render(scene, cam, amb_band=AMB_BAND)
-        e, _ = image_error(images[0], ref["image"], ref["amb"])
+        e, _ = image_error(images[0], ref["image"], ref["flip"])
         assert e <= IMG_TOL
         return
     _check_view(r, sp, scene, cam, 0, mask, seed=5)
@@ -143,12 +138,14 @@ def test_commit_incremental_equals_recompute():
     inc = to_np(r.frozen_sums(0))
     r2, _ = _renderer_for(scene, [cam], m2)
     rec = to_np(r2.frozen_sums(0))
-    ref, amb, _ = oracle.render_sums(scene, cam, subset=~m2.astype(bool), amb_band=AMB_BAND, want_amb=True)
-    keep = amb == 0
+    ab = np.zeros((3, cam["height"], cam["width"]))
+    ref, _, _ = oracle.render_sums(scene, cam, subset=~m2.astype(bool), amb_band=AMB_BAND, amb_sums=ab)
+    # allowance of the near-cut pairs per plane: sum a w max c (P), sum a w (Q), sum a/(1-a) >= |log(1-a)| (log T)
+    allow = [ab[2], ab[2], ab[2], ab[1], ab[0]]
     for k in range(5):
         scale = np.abs(ref[k]).max()
-        assert np.abs(inc[k] - ref[k])[keep].max() <= 1e-5 * scale, k
-        assert np.abs(rec[k] - ref[k])[keep].max() <= 1e-5 * scale, k
+        assert np.max(np.abs(inc[k] - ref[k]) - allow[k]) <= 1e-5 * scale, k
+        assert np.max(np.abs(rec[k] - ref[k]) - allow[k]) <= 1e-5 * scale, k
     # and the active render over the incremental sums still matches the full render
     _check_view(r, sp, scene, cam, 0, m2, seed=9)
 
@@ -236,7 +233,7 @@ def test_state_and_capacity_errors():
     img, _ = small.forward(sp, [cam], [0])
     small.status()
     ref = oracle.render(scene, cam, amb_band=AMB_BAND)
-    assert image_error(img[0], ref["image"], ref["amb"])[0] <= IMG_TOL
+    assert image_error(img[0], ref["image"], ref["flip"])[0] <= IMG_TOL
 
 
 def test_autograd_function_matches_backward():
