@@ -55,6 +55,71 @@ FLOPS_FWD_PER_EVAL = 22
 FLOPS_BWD_PER_EVAL = 39
 
 
+# Source files of each kernel: the DRAM traffic recorded in profiles/dram_traffic.txt is reported
+# only while the digest of these files still matches the one recorded with it.
+KERNEL_SOURCES = {
+    "raster_bwd": ("raster_bwd.cu", "pair_eval.cuh", "common.cuh"),
+    "raster_fwd": ("raster_fwd.cu", "pair_eval.cuh", "common.cuh"),
+    "project": ("project.cu", "common.cuh"),
+    "scatter": ("project.cu", "common.cuh"),
+}
+
+
+def kernel_digest(kernel: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2605_13855_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from profiles/dram_traffic.txt (lines: kernel bytes digest workload),
+    or None when absent or recorded for other sources."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if kernel not in KERNEL_SOURCES or not os.path.exists(path):
+        return None
+    digest = kernel_digest(kernel)
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel and parts[2] == digest:
+            return float(parts[1])
+    return None
+
+
+def algorithmic_bytes(n_active: int, pairs: int, pixels: int, tiles: int) -> dict:
+    """Unique HBM bytes each kernel of one step must move (FP32 parameters: 75 floats = 300 B per
+    splat; screen record 48 B + extent 16 B; 4 B per (splat, tile) pair id; per pixel 20 B of frozen
+    sums, 12 B target, 12 B image, 24 B of pixel state; 40 B of screen-space gradients per splat)."""
+    na, m, p = n_active, pairs, pixels
+    return {
+        "project": na * (4 + 300 + 64) + 4 * tiles,
+        "scan_tiles": 8 * tiles,
+        "scatter": na * (4 + 64) + 4 * m + 4 * tiles,
+        "raster_fwd": 4 * m + 48 * na + p * (20 + 12 + 12 + 24),
+        "raster_bwd": 4 * m + 48 * na + p * 24 + 40 * na,
+        "project_bwd": na * (4 + 300 + 40 + 300),
+    }
+
+
+def hbm_report(per_kernel: dict, n_active: int, pairs: int, pixels: int, tiles: int, ms_step: float,
+               peaks: dict, peak_kind: str) -> dict:
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    ab = algorithmic_bytes(n_active, pairs, pixels, tiles)
+    out = {"peak_gbs": peak, "peak_source": f"hbm_gbs ({peak_kind})", "per_kernel": {}}
+    for k, b in ab.items():
+        if k in per_kernel and per_kernel[k]["avg_ms"] > 0:
+            gbs = b / (per_kernel[k]["avg_ms"] * 1e-3) / 1e9
+            out["per_kernel"][k] = {"bytes": int(b), "gbs": gbs, "frac": gbs / peak}
+    tot = sum(ab.values())
+    out["step_bytes"] = int(tot)
+    out["step_gbs"] = tot / (ms_step * 1e-3) / 1e9
+    out["step_frac"] = out["step_gbs"] / peak
+    out["floor_ms"] = tot / (peak * 1e9) * 1e3
+    return out
+
+
 def fp32_peak_tflops(sm_mhz: float) -> float:
     # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x clock
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -690,11 +755,13 @@ def main():
         if dom in ("raster_bwd", "raster_fwd"):
             ach = flops / avg_s / 1e12
             roofline = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
-                        "frac": ach / peak_tf, "traffic": None,
+                        "frac": ach / peak_tf, "traffic": recorded_traffic(dom),
                         "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (sm_max_mhz of "
                                        f"MEASURED_PEAKS.json, {peak_kind})",
                         "algorithmic": f"E={head['E']} pairs x {FLOPS_BWD_PER_EVAL if dom == 'raster_bwd' else FLOPS_FWD_PER_EVAL} FP32 ops"}
     gpu_launches = 6 * args.steps  # project, scan, scatter, raster_fwd, raster_bwd, project_bwd
+    n_tiles = ((W + 15) // 16) * ((H + 15) // 16)
+    hbm = hbm_report(per_kernel, head["n_active"], head["M"], W * H, n_tiles, ms, peaks, peak_kind)
 
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
@@ -708,6 +775,7 @@ def main():
         "config": {"workload": WORKLOAD, "n_splats": n, "width": W, "height": H,
                    "active_fraction": HEADLINE_FRACTION, "n_active": head["n_active"],
                    "evals_per_step": head["E"], "pairs_per_step": head["M"],
+                   "evals_tile_per_step": 256 * head["M"],
                    "l2": "flushed between timed steps (256 MiB write)", "timing": "CUDA graph replay, CUDA events",
                    "parallelism": f"dp{ws} (one view per rank)"},
         "active_vs_full": None if full is None else {
@@ -721,6 +789,8 @@ def main():
         "stage_update": {"set_active_ms": set_active_ms, "commit_incremental_ms": commit_inc_ms},
         "per_kernel_ms": per_kernel,
         "roofline": roofline,
+        "evals_tile_per_s": 256 * head["M"] / (ms * 1e-3),
+        "hbm": hbm,
         "cpu_baseline": cpu,
         "e2e": None if e2e_ms is None else {
             "value": total_E / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,

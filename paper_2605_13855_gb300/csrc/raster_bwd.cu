@@ -33,15 +33,22 @@ namespace soit {
 // kGroup: before a round of 256 of the tile's splats is split into warps, a
 // shared-memory counting sort orders it by the 4x4-pixel cell of the tile
 // that holds the splat's centre (clamped), so that the 32 splats of a warp
-// tend to cover the same pixels and fewer lanes idle in the per-pixel work.
+// tend to cover the same pixels.
+//
+// Each lane evaluates two adjacent columns per step with paired FP32
+// instructions (f32x2 FMA / multiply / add, one issue slot for two values);
+// the pixel states sit in shared memory as planes so that one 64-bit load
+// fetches a component for both pixels.  Components of the paired operations
+// round exactly like their scalar counterparts, so contribution decisions
+// stay identical to the forward raster's.
 template <bool kGroup>
 __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(const __grid_constant__ Batch b,
                                                               const float4 *__restrict__ rec,
                                                               const int *__restrict__ offsets,
                                                               const uint32_t *__restrict__ pairs, int64_t cap,
                                                               uint32_t nrec, float4 *__restrict__ sgrad) {
-    __shared__ float4 sa[kTilePix];  // g0, g1, g2, A
-    __shared__ float2 sb[kTilePix];  // B, gF
+    // pixel state planes, two adjacent pixels per float2: g0, g1, g2, A, B, -g.F
+    __shared__ float2 sp[6][kTilePix / 2];
     __shared__ uint32_t sorted[kGroup ? kTilePix : 1];
     __shared__ int hist[17];
 
@@ -53,16 +60,16 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(const __grid_const
     const int tid = threadIdx.x;
     {
         const int x = tx * kTile + (tid & (kTile - 1)), y = ty * kTile + (tid >> 4);
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        float2 c = make_float2(0.f, 0.f);
+        float st6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (x < vd.W && y < vd.H) {
             const int64_t HW = (int64_t)vd.W * vd.H, pix = (int64_t)y * vd.W + x;
             const float *st = vd.state;
-            a = make_float4(st[pix], st[HW + pix], st[2 * HW + pix], st[3 * HW + pix]);
-            c = make_float2(st[4 * HW + pix], st[5 * HW + pix]);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) st6[k] = st[k * HW + pix];
+            st6[5] = -st6[5];
         }
-        sa[tid] = a;
-        sb[tid] = c;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) reinterpret_cast<float *>(sp[k])[tid] = st6[k];
     }
     __syncthreads();
 
@@ -120,7 +127,6 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(const __grid_const
         const float rr = a0.z, A2 = a0.w, B2 = a1.x, log2o = a1.y, w = a1.z, yh = a1.w;
         const SplatConsts sc = splat_consts(ox, oy, a0.x, a0.y, rr, A2, log2o);
         const float dy0 = sc.dy0;
-        const float c0 = a2.x, c1 = a2.y, c2 = a2.z;
         // rows of the tile this lane's ellipse can reach; the warp walks their union
         int rlo = kTile, rhi = -1;
         if (valid && yh >= 0.f) {
@@ -130,52 +136,62 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(const __grid_const
         rlo = __reduce_min_sync(0xffffffffu, rlo);
         rhi = __reduce_max_sync(0xffffffffu, rhi);
 
-        float Se = 0.f, Sey = 0.f, See = 0.f, Sd = 0.f, Sdy = 0.f, Sdyy = 0.f, gw = 0.f;
-        float gc0 = 0.f, gc1 = 0.f, gc2 = 0.f;
+        const float2 A2p = make_float2(A2, A2), wp = make_float2(w, w);
+        const float2 c0p = make_float2(a2.x, a2.x), c1p = make_float2(a2.y, a2.y), c2p = make_float2(a2.z, a2.z);
+        const float2 zero2 = make_float2(0.f, 0.f);
+        float2 See = zero2, gw = zero2, gc0 = zero2, gc1 = zero2, gc2 = zero2;
+        float Se = 0.f, Sey = 0.f, Sd = 0.f, Sdy = 0.f, Sdyy = 0.f;
         for (int ky = rlo; ky <= rhi; ++ky) {
             const RowTerms rt = row_terms(sc.A2dx0, dy0, sc.rA2, B2, ky);
-            float Rd = 0.f, Re = 0.f;
+            const float2 e10p = make_float2(rt.e10, rt.e10), e2p = make_float2(rt.e2sq, rt.e2sq);
+            float2 Rd = zero2, Re = zero2;
 #pragma unroll
-            for (int kx = 0; kx < kTile; ++kx) {
-                const float e1 = col_e1(A2, rt.e10, kx);
-                const float sq = quad_s(e1, rt.e2sq);
-                if (sq <= sc.thr) {
-                    const int k = ky * kTile + kx;
-                    const float4 p = sa[k];
-                    const float2 pb = sb[k];
-                    const float ar = fast_exp2(log2o - sq);
-                    const float a = fminf(ar, kAlphaMax);
-                    const float gcd = fmaf(p.x, c0, fmaf(p.y, c1, fmaf(p.z, c2, -pb.y)));  // g.c - g.F
-                    const float Ba = pb.x * a;
-                    const float dLda = fmaf(p.w, fast_rcp(1.f - a), w * (pb.x * gcd));
-                    gw = fmaf(Ba, gcd, gw);
-                    gc0 = fmaf(Ba, p.x, gc0);  // times w in the epilogue
-                    gc1 = fmaf(Ba, p.y, gc1);
-                    gc2 = fmaf(Ba, p.z, gc2);
-                    const float da = dLda * (ar > kAlphaMax ? 0.f : a);
-                    Rd += da;
-                    const float qd = da * e1;
-                    Re += qd;
-                    See = fmaf(qd, e1, See);
+            for (int kp = 0; kp < kTile / 2; ++kp) {
+                const float2 e1 = __ffma2_rn(A2p, make_float2((float)(2 * kp), (float)(2 * kp + 1)), e10p);
+                const float2 sq = __ffma2_rn(e1, e1, e2p);
+                const bool in0 = sq.x <= sc.thr, in1 = sq.y <= sc.thr;
+                if (in0 || in1) {
+                    const int kk = ky * (kTile / 2) + kp;
+                    const float2 g0 = sp[0][kk], g1 = sp[1][kk], g2 = sp[2][kk];
+                    const float2 Ap = sp[3][kk], Bp = sp[4][kk], nF = sp[5][kk];
+                    const float ar0 = fast_exp2(log2o - sq.x), ar1 = fast_exp2(log2o - sq.y);
+                    const float2 a = make_float2(in0 ? fminf(ar0, kAlphaMax) : 0.f, in1 ? fminf(ar1, kAlphaMax) : 0.f);
+                    // the alpha path (o, mu', conic) is off where alpha is clamped
+                    const float2 am = make_float2(ar0 > kAlphaMax ? 0.f : a.x, ar1 > kAlphaMax ? 0.f : a.y);
+                    const float2 gcd = __ffma2_rn(g0, c0p, __ffma2_rn(g1, c1p, __ffma2_rn(g2, c2p, nF)));  // g.c - g.F
+                    const float2 Ba = __fmul2_rn(Bp, a);
+                    const float2 inv = make_float2(fast_rcp(1.f - a.x), fast_rcp(1.f - a.y));
+                    const float2 dLda = __ffma2_rn(Ap, inv, __fmul2_rn(wp, __fmul2_rn(Bp, gcd)));
+                    gw = __ffma2_rn(Ba, gcd, gw);
+                    gc0 = __ffma2_rn(Ba, g0, gc0);  // times w in the epilogue
+                    gc1 = __ffma2_rn(Ba, g1, gc1);
+                    gc2 = __ffma2_rn(Ba, g2, gc2);
+                    const float2 da = __fmul2_rn(dLda, am);
+                    Rd = __fadd2_rn(Rd, da);
+                    const float2 qd = __fmul2_rn(da, e1);
+                    Re = __fadd2_rn(Re, qd);
+                    See = __ffma2_rn(qd, e1, See);
                 }
             }
-            Sd += Rd;
-            Sdy = fmaf(Rd, rt.dy, Sdy);
-            Sdyy = fmaf(Rd, rt.dy * rt.dy, Sdyy);
-            Se += Re;
-            Sey = fmaf(Re, rt.dy, Sey);
+            const float rd = Rd.x + Rd.y, re = Re.x + Re.y;
+            Sd += rd;
+            Sdy = fmaf(rd, rt.dy, Sdy);
+            Sdyy = fmaf(rd, rt.dy * rt.dy, Sdyy);
+            Se += re;
+            Sey = fmaf(re, rt.dy, Sey);
         }
         if (valid) {
             const float K = -2.f * kLn2;
+            const float See1 = See.x + See.y;
             const float g_mx = -K * A2 * Se;
             const float g_my = K * (A2 * rr * Se - B2 * B2 * Sdy);
             const float g_r = -K * A2 * Sey;
-            const float g_A2 = K * See / A2;
+            const float g_A2 = K * See1 / A2;
             const float g_B2 = K * B2 * Sdyy;
             float4 *out = sgrad + 3 * (int64_t)q;
             atomicAdd(out + 0, make_float4(g_mx, g_my, g_r, g_A2));
-            atomicAdd(out + 1, make_float4(g_B2, Sd, gw, w * gc0));
-            atomicAdd(reinterpret_cast<float2 *>(out + 2), make_float2(w * gc1, w * gc2));
+            atomicAdd(out + 1, make_float4(g_B2, Sd, gw.x + gw.y, w * (gc0.x + gc0.y)));
+            atomicAdd(reinterpret_cast<float2 *>(out + 2), make_float2(w * (gc1.x + gc1.y), w * (gc2.x + gc2.y)));
         }
     }
 }

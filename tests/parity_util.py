@@ -25,7 +25,7 @@ import oracle
 IMG_TOL = 1e-5
 GRAD_TOL = 1e-4
 AMB_BAND = 3e-4
-AMB_PIX_MAX = 0.05  # cap on the fraction of pixels whose allowance exceeds the tolerance itself
+AMB_PIX_MAX = 0.01  # cap on the fraction of pixels that pass only through their allowance
 
 GROUPS = dict(means=(0, 3), quats=(3, 7), log_scales=(7, 10), opacity_logits=(10, 11), sh_color=(11, 59),
               sh_weight=(59, 75))
@@ -37,14 +37,19 @@ def to_np(t):
 
 def image_error(img_gpu, ref_img, flip=None):
     """(max over pixels of (|C_gpu - C_ref| - flip)^+ / max|C_ref|, fraction of pixels whose
-    allowance flip exceeds IMG_TOL max|C_ref|, i.e. where the check is looser than the tolerance)."""
+    error exceeds IMG_TOL max|C_ref| without the allowance, i.e. that pass only through it).
+
+    The fraction of pixels merely *carrying* an allowance grows with the number of pairs per
+    pixel (about AMB_BAND per pair: the cutoff ellipse's area is proportional to the
+    exponent), so at a million splats most pixels carry one; the bar is on the pixels that
+    use it."""
     a = to_np(img_gpu) if isinstance(img_gpu, torch.Tensor) else img_gpu
     scale = max(np.abs(ref_img).max(), 1e-30)
     d = np.abs(a - ref_img).max(axis=2)
     frac = 0.0
     if flip is not None:
+        frac = float((d > IMG_TOL * scale).mean())
         d = np.maximum(d - flip, 0.0)
-        frac = float((flip > IMG_TOL * scale).mean())
     return float(d.max(initial=0.0) / scale), frac
 
 
