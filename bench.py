@@ -536,6 +536,7 @@ def main():
     ap.add_argument("--fwd-strip", type=int, default=0, help="forward raster pixels per thread (1, 2, 4; 0 = default)")
     ap.add_argument("--proj-lanes", type=int, default=0, help="projection lanes per splat (4, 16; 0 = default)")
     ap.add_argument("--bwd-group", type=int, default=0, help="backward grouping by centre cell (1 on, -1 off, 0 default)")
+    ap.add_argument("--tile-order", type=int, default=0, help="rasters take tiles heaviest first (1 on, -1 off, 0 default)")
     ap.add_argument("--workload", default="unbounded", choices=["unbounded", "batched", "precision"],
                     help="unbounded (default line): 1M splats, one view; batched: 3M splats, 16 views; "
                          "precision: 3M splats, 8 views, BF16 vs FP32 SH")
@@ -587,7 +588,8 @@ def main():
         return torch.as_tensor(m, device=dev)
 
     r = Renderer(n, [(W, H)], max_pairs=1 << 27, fwd_pixels_per_thread=args.fwd_strip,
-                 proj_lanes_per_splat=args.proj_lanes, bwd_group_by_cell=args.bwd_group)
+                 proj_lanes_per_splat=args.proj_lanes, bwd_group_by_cell=args.bwd_group,
+                 raster_tile_order=args.tile_order)
     img = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
     loss = torch.empty(1, dtype=torch.float32, device=dev)
 

@@ -136,7 +136,11 @@ typedef struct {
                                       tile's splats by the 4x4-pixel cell of
                                       their centre before assigning warps;
                                       1 = on, -1 = off, 0 = default (off)      */
-    int32_t reserved[3];
+    int32_t raster_tile_order;     /* rasters take tiles heaviest first (tiles
+                                      ranked by pair count in four classes per
+                                      octave) instead of in index order;
+                                      1 = on, -1 = off, 0 = default (on)       */
+    int32_t reserved[2];
 } sparseoit_config;
 
 /* Create a context for a scene of max_splats splats and n_views training

@@ -70,7 +70,7 @@ class Tuning(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("max_pairs", ctypes.c_int64), ("fwd_pixels_per_thread", ctypes.c_int32),
                 ("proj_lanes_per_splat", ctypes.c_int32), ("bwd_group_by_cell", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("raster_tile_order", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 _lock = threading.Lock()

@@ -25,6 +25,7 @@ struct sparseoit_ctx {
     int fwd_strip = 4;            // pixels per thread of the forward raster
     int proj_lanes = 4;           // lanes per splat of the projection
     bool bwd_group = false;       // backward: group a tile's splats by centre cell
+    bool tile_order = true;       // rasters take tiles heaviest first
     std::string err;
 
     // active set
@@ -43,7 +44,7 @@ struct sparseoit_ctx {
     // batch workspace
     float4 *d_rec = nullptr, *d_ext = nullptr;
     int64_t rec_cap = 0;          // records
-    int *d_tile_count = nullptr, *d_offsets = nullptr, *d_cursor = nullptr;
+    int *d_tile_count = nullptr, *d_offsets = nullptr, *d_cursor = nullptr, *d_order = nullptr;
     int64_t tile_cap = 0;
     uint32_t *d_pairs = nullptr;
     std::vector<float *> d_state;  // per batch slot, 6 planes of the largest view
@@ -187,6 +188,7 @@ static int render_pass_bin(sparseoit_ctx *ctx, Batch &b, const sparseoit_splats 
                            const int *list2, int n2, cudaStream_t st) {
     const int64_t nrec = (int64_t)b.n_views * (n1 + n2);
     if (nrec > 0xffffffffll) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "too many records in one batch");
+    b.tile_order = ctx->tile_order ? ctx->d_order : nullptr;
     if (ctx->rec_cap < 3 * nrec || ctx->tile_cap < (int64_t)b.total_tiles + 1)
         return fail(ctx, SPARSEOIT_ERR_STATE, "batch workspace not sized");
     CK(cudaMemsetAsync(ctx->d_tile_count, 0, (size_t)b.total_tiles * sizeof(int), st), "memset(tile counts)");
@@ -199,8 +201,8 @@ static int render_pass_bin(sparseoit_ctx *ctx, Batch &b, const sparseoit_splats 
     CK_LAUNCH("project_kernel");
     {
         ProfScope ps(ctx, "scan_tiles", st);
-        launch_scan_tiles(ctx->d_tile_count, b.total_tiles, ctx->d_offsets, ctx->d_cursor, ctx->pair_cap,
-                          ctx->d_status, ctx->d_npairs, st);
+        launch_scan_tiles(ctx->d_tile_count, b.total_tiles, ctx->d_offsets, ctx->d_cursor, b.tile_order ? ctx->d_order : nullptr,
+                          ctx->pair_cap, ctx->d_status, ctx->d_npairs, st);
     }
     CK_LAUNCH("scan_tiles_kernel");
     {
@@ -228,12 +230,14 @@ static int ensure_batch_ws(sparseoit_ctx *ctx, int64_t nrec, int64_t tiles) {
         if (ctx->d_tile_count) cudaFree(ctx->d_tile_count);
         if (ctx->d_offsets) cudaFree(ctx->d_offsets);
         if (ctx->d_cursor) cudaFree(ctx->d_cursor);
-        ctx->d_tile_count = ctx->d_offsets = ctx->d_cursor = nullptr;
+        if (ctx->d_order) cudaFree(ctx->d_order);
+        ctx->d_tile_count = ctx->d_offsets = ctx->d_cursor = ctx->d_order = nullptr;
         ctx->tile_cap = 0;
         const int64_t n = tiles + 1;
         CK(cudaMalloc((void **)&ctx->d_tile_count, (size_t)n * sizeof(int)), "cudaMalloc(tile counts)");
         CK(cudaMalloc((void **)&ctx->d_offsets, (size_t)n * sizeof(int)), "cudaMalloc(tile offsets)");
         CK(cudaMalloc((void **)&ctx->d_cursor, (size_t)n * sizeof(int)), "cudaMalloc(tile cursors)");
+        CK(cudaMalloc((void **)&ctx->d_order, (size_t)n * sizeof(int)), "cudaMalloc(tile order)");
         ctx->tile_cap = n;
     }
     return SPARSEOIT_OK;
@@ -279,6 +283,7 @@ int sparseoit_create(sparseoit_ctx **out, int64_t max_splats, int32_t n_views, c
         ctx->proj_lanes = l;
     }
     if (cfg && cfg->bwd_group_by_cell != 0) ctx->bwd_group = cfg->bwd_group_by_cell > 0;
+    if (cfg && cfg->raster_tile_order != 0) ctx->tile_order = cfg->raster_tile_order > 0;
     if (ctx->pair_cap > 0x7fffffffll) ctx->pair_cap = 0x7fffffffll;
     ctx->view_gen.assign(n_views, -1);
     ctx->d_frozen.assign(n_views, nullptr);
@@ -329,7 +334,7 @@ int sparseoit_destroy(sparseoit_ctx *ctx) {
     for (float *p : ctx->d_state) if (p) cudaFree(p);
     void *bufs[] = {ctx->d_mask[0], ctx->d_mask[1], ctx->d_idx_active, ctx->d_idx_comp, ctx->d_idx_plus,
                     ctx->d_idx_minus, ctx->d_blk, ctx->d_totals, ctx->d_rec, ctx->d_ext, ctx->d_tile_count,
-                    ctx->d_offsets, ctx->d_cursor, ctx->d_pairs, ctx->d_sgrad, ctx->d_status, ctx->d_npairs,
+                    ctx->d_offsets, ctx->d_cursor, ctx->d_order, ctx->d_pairs, ctx->d_sgrad, ctx->d_status, ctx->d_npairs,
                     ctx->d_contrib};
     for (void *p : bufs) if (p) cudaFree(p);
     if (ctx->h_totals) cudaFreeHost(ctx->h_totals);

@@ -57,8 +57,15 @@ struct Batch {
     int total_tiles;
     int n_list;                   // list entries (records) per view
     int pad_;
+    const int *tile_order;        // raster block -> global tile (heaviest first); null = identity
     ViewDesc v[kMaxViews];
 };
+
+// Global tile a raster block works on: blocks are handed out heaviest tile
+// first, so that the long tiles start early instead of forming the tail.
+__device__ __forceinline__ int block_tile(const Batch &b) {
+    return b.tile_order ? __ldg(b.tile_order + blockIdx.x) : (int)blockIdx.x;
+}
 
 struct SplatPtrs {
     const float *means, *quats, *log_scales, *opacity_logits;

@@ -7,8 +7,9 @@ namespace soit {
 // lanes = lanes per splat of the projection (4 or 16).
 int launch_project(const Batch &b, const SplatPtrs &sp, bool bf16, int lanes, const int *list1, int n1,
                    const int *list2, int n2, float4 *rec, float4 *ext, int *tile_count, cudaStream_t st);
-int launch_scan_tiles(const int *count, int total, int *offsets, int *cursor, int64_t cap, unsigned *status,
-                      int64_t *pairs_out, cudaStream_t st);
+// order (nullable): receives the raster blocks' tile order, heaviest load class first.
+int launch_scan_tiles(const int *count, int total, int *offsets, int *cursor, int *order, int64_t cap,
+                      unsigned *status, int64_t *pairs_out, cudaStream_t st);
 int launch_scatter(const Batch &b, const float4 *rec, const float4 *ext, int *cursor, uint32_t *pairs, int64_t cap,
                    cudaStream_t st);
 

@@ -169,11 +169,28 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Ba
 // Exclusive scan of the tile counts of the batch by one block of 1024
 // threads, 8 consecutive counts per thread per chunk.  offsets[total] = M.
 // cursor[t] = offsets[t] for the scatter.  Flags kStatusCapacity if M > cap.
+// Load class of a tile with c pairs: 0 for an empty tile, else 1 + 4 e + m
+// for c = 2^e (1 + m/4 + ...), i.e. four classes per octave (<= 124).
+constexpr int kLoadClasses = 128;
+__device__ __forceinline__ int load_class(int c) {
+    if (c <= 0) return 0;
+    const int e = 31 - __clz(c);
+    const int m = (e >= 2 ? (c >> (e - 2)) : (c << (2 - e))) & 3;
+    return 1 + 4 * e + m;
+}
+
+// One block: exclusive scan of the per-tile pair counts into offsets (and
+// the scatter cursors), the capacity check, and, when order is given, the
+// order in which the raster blocks take the tiles: by load class, heaviest
+// first (a bucketed longest-processing-time-first schedule; the order
+// within a class is arbitrary and changes no result).
 __global__ void __launch_bounds__(1024) scan_tiles_kernel(const int *__restrict__ count, int total,
                                                           int *__restrict__ offsets, int *__restrict__ cursor,
-                                                          int64_t cap, unsigned *status, int64_t *pairs_out) {
+                                                          int *__restrict__ order, int64_t cap, unsigned *status,
+                                                          int64_t *pairs_out) {
     __shared__ int warp_sums[32];
     __shared__ int carry_s;
+    __shared__ int cls_pos[kLoadClasses];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) carry_s = 0;
     __syncthreads();
@@ -224,6 +241,21 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(const int *__restrict_
         if (pairs_out) *pairs_out = carry_s;
         if ((int64_t)carry_s > cap) atomicOr(status, kStatusCapacity);
     }
+    if (!order) return;
+    for (int k = tid; k < kLoadClasses; k += 1024) cls_pos[k] = 0;
+    __syncthreads();
+    for (int i = tid; i < total; i += 1024) atomicAdd(&cls_pos[load_class(count[i])], 1);
+    __syncthreads();
+    if (tid == 0) {  // first position of each class, heaviest class first
+        int run = 0;
+        for (int k = kLoadClasses - 1; k >= 0; --k) {
+            const int h = cls_pos[k];
+            cls_pos[k] = run;
+            run += h;
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < total; i += 1024) order[atomicAdd(&cls_pos[load_class(count[i])], 1)] = i;
 }
 
 // One warp per list entry.  Lanes compute the column range of one tile row
@@ -305,9 +337,9 @@ int launch_project(const Batch &b, const SplatPtrs &sp, bool bf16, int lanes, co
     return 0;
 }
 
-int launch_scan_tiles(const int *count, int total, int *offsets, int *cursor, int64_t cap, unsigned *status,
-                      int64_t *pairs_out, cudaStream_t st) {
-    scan_tiles_kernel<<<1, 1024, 0, st>>>(count, total, offsets, cursor, cap, status, pairs_out);
+int launch_scan_tiles(const int *count, int total, int *offsets, int *cursor, int *order, int64_t cap,
+                      unsigned *status, int64_t *pairs_out, cudaStream_t st) {
+    scan_tiles_kernel<<<1, 1024, 0, st>>>(count, total, offsets, cursor, order, cap, status, pairs_out);
     return 0;
 }
 

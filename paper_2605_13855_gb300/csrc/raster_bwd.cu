@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(const __grid_const
     __shared__ uint32_t sorted[kGroup ? kTilePix : 1];
     __shared__ int hist[17];
 
-    const int gt = blockIdx.x;
+    const int gt = block_tile(b);
     const int v = find_view(b, gt);
     const ViewDesc &vd = b.v[v];
     const int lt = gt - vd.tile_base;

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
     __shared__ float red[kFwdThreads / 32];
     __shared__ unsigned red_n[kFwdThreads / 32];
 
-    const int gt = blockIdx.x;
+    const int gt = block_tile(b);
     const int v = find_view(b, gt);
     const ViewDesc &vd = b.v[v];
     const int lt = gt - vd.tile_base;

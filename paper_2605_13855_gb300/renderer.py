@@ -112,7 +112,8 @@ class Renderer:
     """A SparseOIT context: active set, per-view frozen sums, batched fwd / bwd."""
 
     def __init__(self, n_splats: int, view_sizes: Sequence[Sequence[int]], max_pairs: int = 0,
-                 fwd_pixels_per_thread: int = 0, proj_lanes_per_splat: int = 0, bwd_group_by_cell: int = 0):
+                 fwd_pixels_per_thread: int = 0, proj_lanes_per_splat: int = 0, bwd_group_by_cell: int = 0,
+                 raster_tile_order: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("sparseoit needs a CUDA device")
         self.lib = _lib.load()
@@ -126,6 +127,7 @@ class Renderer:
         cfg.fwd_pixels_per_thread = int(fwd_pixels_per_thread)
         cfg.proj_lanes_per_splat = int(proj_lanes_per_splat)
         cfg.bwd_group_by_cell = int(bwd_group_by_cell)
+        cfg.raster_tile_order = int(raster_tile_order)
         self._ctx = ctypes.c_void_p()
         rc = self.lib.sparseoit_create(ctypes.byref(self._ctx), self.n, nv, ws, hs, ctypes.byref(cfg))
         if rc != _lib.OK:
