@@ -48,11 +48,11 @@ def _peaks():
 # FP32 flops (an FMA counts 2, exp2 / reciprocal / min 1 each) of one
 # contributing (splat, pixel) pair in the algorithm the kernels run: forward
 # 22 = offsets 2, u 2, e1 1, e2 1, s 3, log2 alpha 1, exp2 1, clamp 1,
-# P 6, Q 2, T 2; backward 39 = the same 12 up to the clamp, g.c - g.F 6,
-# B (g.c - g.F) 1, 1 - a 1, reciprocal 1, dL/da 3, B a 1, dL/dw 2,
-# dL/dc 6, da 1, chain sums 6.
+# P 6, Q 2, T 2; backward 38 = the same 12 up to the clamp,
+# D = (B g).c - B g.F 6, 1 - a 1, reciprocal 1, dL/da = A/(1 - a) + w D 3,
+# dL/dw += a D 2, dL/dc += a (B g) 6, da 1, chain sums 6.
 FLOPS_FWD_PER_EVAL = 22
-FLOPS_BWD_PER_EVAL = 39
+FLOPS_BWD_PER_EVAL = 38
 
 
 # Source files of each kernel: the DRAM traffic recorded in profiles/dram_traffic.txt is reported

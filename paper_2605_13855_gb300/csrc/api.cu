@@ -47,7 +47,7 @@ struct sparseoit_ctx {
     int *d_tile_count = nullptr, *d_offsets = nullptr, *d_cursor = nullptr, *d_order = nullptr;
     int64_t tile_cap = 0;
     uint32_t *d_pairs = nullptr;
-    std::vector<float *> d_state;  // per batch slot, 6 planes of the largest view
+    std::vector<float *> d_state;  // per batch slot, 5 planes of the largest view
     int64_t max_pix = 0;
     float4 *d_sgrad = nullptr;
     int64_t sgrad_cap = 0;        // records
@@ -467,7 +467,7 @@ int sparseoit_forward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const 
     b.n_list = (int)ctx->n_active;
     while ((int)ctx->d_state.size() < n_views) ctx->d_state.push_back(nullptr);
     for (int k = 0; k < n_views; ++k) {
-        if (!ctx->d_state[k]) CK(cudaMalloc((void **)&ctx->d_state[k], (size_t)(6 * ctx->max_pix) * sizeof(float)),
+        if (!ctx->d_state[k]) CK(cudaMalloc((void **)&ctx->d_state[k], (size_t)(5 * ctx->max_pix) * sizeof(float)),
                                  "cudaMalloc(pixel state)");
         b.v[k].state = ctx->d_state[k];
     }

@@ -10,7 +10,7 @@
 //     [tile_base, tile_base + tiles_x * tiles_y)); offsets[t] .. offsets[t+1]
 //     index the u32 pair arena that holds record indices q (no depth key).
 //   * per-pixel planes (H*W floats each): frozen sums (P_r, P_g, P_b, Q, log T)
-//     and the backward pixel state (g_r, g_g, g_b, A, B, g.F).
+//     and the backward pixel state (B g_r, B g_g, B g_b, A, -B g.F).
 //
 // The per-pair exponent is evaluated in a factored form of Eq. 5 that has no
 // cancellation for thin ellipses:  with Sigma' = [[sxx, sxy], [sxy, syy]],
@@ -48,7 +48,7 @@ struct ViewDesc {
     float *image;                 // [H, W, 3] output image (forward)
     const float *target;          // [H, W, 3] L1 target (fused loss) or null
     float *frozen;                // 5 planes: frozen sums of this view
-    float *state;                 // 6 planes: pixel state (or F, T, Q before prep)
+    float *state;                 // 5 planes: pixel state (or F, T, Q before prep)
     const float *grad_image;      // [H, W, 3] dL/dC (unfused backward) or null
 };
 

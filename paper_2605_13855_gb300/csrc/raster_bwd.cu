@@ -8,10 +8,10 @@
 // the tile with its splat's full tile gradient in registers, added with one
 // vector atomic per 4 fields.  No pair is evaluated twice.
 //
-// Per pixel state (g = dL/dC): A = T g.(F - c0), B = (1 - T)/Q (0 if Q = 0),
-// gF = g.F.  Eq. 10 contracted with g gives, per pair,
-//   dL/da = A/(1 - a) + B w (g.c - gF),  dL/dw = B a (g.c - gF),
-//   dL/dc = B a w g,
+// Per pixel state (g = dL/dC), five planes: B g (3), A = T g.(F - c0) and
+// -B g.F, with B = (1 - T)/Q (0 if Q = 0).  Eq. 10 contracted with g gives,
+// per pair, with D = B (g.c - g.F) = (B g).c + (-B g.F),
+//   dL/da = A/(1 - a) + w D,  dL/dw = a D,  dL/dc = w a (B g),
 // and, unless a is clamped at 0.99, dL/d(ln o) = a dL/da and
 // dL/ds = -ln2 a dL/da, chained to (mu'x, mu'y, r, A2, B2) below.  Each warp
 // walks only the tile rows that some lane's ellipse reaches.
@@ -47,8 +47,8 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(const __grid_const
                                                               const int *__restrict__ offsets,
                                                               const uint32_t *__restrict__ pairs, int64_t cap,
                                                               uint32_t nrec, float4 *__restrict__ sgrad) {
-    // pixel state planes, two adjacent pixels per float2: g0, g1, g2, A, B, -g.F
-    __shared__ float2 sp[6][kTilePix / 2];
+    // pixel state planes, two adjacent pixels per float2: B g0, B g1, B g2, A, -B g.F
+    __shared__ float2 sp[5][kTilePix / 2];
     __shared__ uint32_t sorted[kGroup ? kTilePix : 1];
     __shared__ int hist[17];
 
@@ -60,16 +60,15 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(const __grid_const
     const int tid = threadIdx.x;
     {
         const int x = tx * kTile + (tid & (kTile - 1)), y = ty * kTile + (tid >> 4);
-        float st6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float st5[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
         if (x < vd.W && y < vd.H) {
             const int64_t HW = (int64_t)vd.W * vd.H, pix = (int64_t)y * vd.W + x;
             const float *st = vd.state;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) st6[k] = st[k * HW + pix];
-            st6[5] = -st6[5];
+            for (int k = 0; k < 5; ++k) st5[k] = st[k * HW + pix];
         }
 #pragma unroll
-        for (int k = 0; k < 6; ++k) reinterpret_cast<float *>(sp[k])[tid] = st6[k];
+        for (int k = 0; k < 5; ++k) reinterpret_cast<float *>(sp[k])[tid] = st5[k];
     }
     __syncthreads();
 
@@ -136,7 +135,8 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(const __grid_const
         rlo = __reduce_min_sync(0xffffffffu, rlo);
         rhi = __reduce_max_sync(0xffffffffu, rhi);
 
-        const float2 A2p = make_float2(A2, A2), wp = make_float2(w, w);
+        const float2 A2p = make_float2(A2, A2), wp = make_float2(w, w), l2op = make_float2(log2o, log2o);
+        const float2 m1 = make_float2(-1.f, -1.f), one2 = make_float2(1.f, 1.f);
         const float2 c0p = make_float2(a2.x, a2.x), c1p = make_float2(a2.y, a2.y), c2p = make_float2(a2.z, a2.z);
         const float2 zero2 = make_float2(0.f, 0.f);
         float2 See = zero2, gw = zero2, gc0 = zero2, gc1 = zero2, gc2 = zero2;
@@ -152,20 +152,22 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(const __grid_const
                 const bool in0 = sq.x <= sc.thr, in1 = sq.y <= sc.thr;
                 if (in0 || in1) {
                     const int kk = ky * (kTile / 2) + kp;
-                    const float2 g0 = sp[0][kk], g1 = sp[1][kk], g2 = sp[2][kk];
-                    const float2 Ap = sp[3][kk], Bp = sp[4][kk], nF = sp[5][kk];
-                    const float ar0 = fast_exp2(log2o - sq.x), ar1 = fast_exp2(log2o - sq.y);
+                    const float2 b0 = sp[0][kk], b1 = sp[1][kk], b2 = sp[2][kk];
+                    const float2 Ap = sp[3][kk], nbF = sp[4][kk];
+                    // log2 o - s: -s + log2 o rounds once, exactly like the forward's subtraction
+                    const float2 lg = __ffma2_rn(sq, m1, l2op);
+                    const float ar0 = fast_exp2(lg.x), ar1 = fast_exp2(lg.y);
                     const float2 a = make_float2(in0 ? fminf(ar0, kAlphaMax) : 0.f, in1 ? fminf(ar1, kAlphaMax) : 0.f);
                     // the alpha path (o, mu', conic) is off where alpha is clamped
                     const float2 am = make_float2(ar0 > kAlphaMax ? 0.f : a.x, ar1 > kAlphaMax ? 0.f : a.y);
-                    const float2 gcd = __ffma2_rn(g0, c0p, __ffma2_rn(g1, c1p, __ffma2_rn(g2, c2p, nF)));  // g.c - g.F
-                    const float2 Ba = __fmul2_rn(Bp, a);
-                    const float2 inv = make_float2(fast_rcp(1.f - a.x), fast_rcp(1.f - a.y));
-                    const float2 dLda = __ffma2_rn(Ap, inv, __fmul2_rn(wp, __fmul2_rn(Bp, gcd)));
-                    gw = __ffma2_rn(Ba, gcd, gw);
-                    gc0 = __ffma2_rn(Ba, g0, gc0);  // times w in the epilogue
-                    gc1 = __ffma2_rn(Ba, g1, gc1);
-                    gc2 = __ffma2_rn(Ba, g2, gc2);
+                    const float2 D = __ffma2_rn(b0, c0p, __ffma2_rn(b1, c1p, __ffma2_rn(b2, c2p, nbF)));  // B (g.c - g.F)
+                    const float2 oma = __ffma2_rn(a, m1, one2);                                            // 1 - a
+                    const float2 inv = make_float2(fast_rcp(oma.x), fast_rcp(oma.y));
+                    const float2 dLda = __ffma2_rn(Ap, inv, __fmul2_rn(wp, D));
+                    gw = __ffma2_rn(a, D, gw);
+                    gc0 = __ffma2_rn(a, b0, gc0);  // times w in the epilogue
+                    gc1 = __ffma2_rn(a, b1, gc1);
+                    gc2 = __ffma2_rn(a, b2, gc2);
                     const float2 da = __fmul2_rn(dLda, am);
                     Rd = __fadd2_rn(Rd, da);
                     const float2 qd = __fmul2_rn(da, e1);
@@ -209,12 +211,12 @@ __global__ void prep_state_kernel(const __grid_constant__ Batch b, float bg0, fl
         const float F0 = st[pix], F1 = st[HW + pix], F2 = st[2 * HW + pix], T = st[3 * HW + pix], Q = st[4 * HW + pix];
         const float *gi = vd.grad_image + 3 * pix;
         const float g0 = gi[0], g1 = gi[1], g2 = gi[2];
-        st[pix] = g0;
-        st[HW + pix] = g1;
-        st[2 * HW + pix] = g2;
+        const float B = Q > 0.f ? (1.f - T) / Q : 0.f;
+        st[pix] = B * g0;
+        st[HW + pix] = B * g1;
+        st[2 * HW + pix] = B * g2;
         st[3 * HW + pix] = T * (g0 * (F0 - bg0) + g1 * (F1 - bg1) + g2 * (F2 - bg2));
-        st[4 * HW + pix] = Q > 0.f ? (1.f - T) / Q : 0.f;
-        st[5 * HW + pix] = g0 * F0 + g1 * F1 + g2 * F2;
+        st[4 * HW + pix] = -B * (g0 * F0 + g1 * F1 + g2 * F2);
     }
 }
 

@@ -163,12 +163,12 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
                 const float g0 = d0 > 0.f ? inv3hw : (d0 < 0.f ? -inv3hw : 0.f);
                 const float g1 = d1 > 0.f ? inv3hw : (d1 < 0.f ? -inv3hw : 0.f);
                 const float g2 = d2 > 0.f ? inv3hw : (d2 < 0.f ? -inv3hw : 0.f);
-                st[pix] = g0;
-                st[HW + pix] = g1;
-                st[2 * HW + pix] = g2;
+                const float B = omT * invQ;
+                st[pix] = B * g0;
+                st[HW + pix] = B * g1;
+                st[2 * HW + pix] = B * g2;
                 st[3 * HW + pix] = Tt * (g0 * (F0 - bg0) + g1 * (F1 - bg1) + g2 * (F2 - bg2));
-                st[4 * HW + pix] = omT * invQ;
-                st[5 * HW + pix] = g0 * F0 + g1 * F1 + g2 * F2;
+                st[4 * HW + pix] = -B * (g0 * F0 + g1 * F1 + g2 * F2);
             } else {
                 st[pix] = F0;
                 st[HW + pix] = F1;
