@@ -91,14 +91,14 @@ def recorded_traffic(kernel: str):
 def algorithmic_bytes(n_active: int, pairs: int, pixels: int, tiles: int) -> dict:
     """Unique HBM bytes each kernel of one step must move (FP32 parameters: 75 floats = 300 B per
     splat; screen record 48 B + extent 16 B; 4 B per (splat, tile) pair id; per pixel 20 B of frozen
-    sums, 12 B target, 12 B image, 24 B of pixel state; 40 B of screen-space gradients per splat)."""
+    sums, 12 B target, 12 B image, 20 B of pixel state; 40 B of screen-space gradients per splat)."""
     na, m, p = n_active, pairs, pixels
     return {
         "project": na * (4 + 300 + 64) + 4 * tiles,
         "scan_tiles": 8 * tiles,
         "scatter": na * (4 + 64) + 4 * m + 4 * tiles,
-        "raster_fwd": 4 * m + 48 * na + p * (20 + 12 + 12 + 24),
-        "raster_bwd": 4 * m + 48 * na + p * 24 + 40 * na,
+        "raster_fwd": 4 * m + 48 * na + p * (20 + 12 + 12 + 20),
+        "raster_bwd": 4 * m + 48 * na + p * 20 + 40 * na,
         "project_bwd": na * (4 + 300 + 40 + 300),
     }
 
@@ -404,6 +404,64 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_active_update(args):
+    """The periodic active-set update of Alg. 1 (sparseoit_update_active_set): 1M splats (unbounded
+    scene), 60 training views of 1297x840, 30 picked by farthest point sampling, full-set fwd+bwd
+    with the fused L1 loss on each, gradients summed, Eq. 8 against per-group thresholds."""
+    import torch
+    import __graft_entry__
+    from paper_2605_13855_gb300 import scenes
+    from paper_2605_13855_gb300.renderer import Renderer, SplatParams, activeness
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    c = scenes.ACTIVE_UPDATE
+    n, W, H, V, S = c["n"], c["width"], c["height"], c["views"], c["n_sub"]
+    scene = scenes.unbounded_scene(n, c["seed"])
+    cams = scenes.training_cameras(V, c["camera_seed"], W, H)
+    rng = np.random.default_rng(c["camera_seed"] + 1)
+    sp = SplatParams.from_numpy(scene, device=dev)
+    targets = [torch.as_tensor(scenes.uniform_target(c["camera_seed"] + 100 + k, W, H), device=dev) for k in range(V)]
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        r = Renderer(n, [(W, H)] * V, max_pairs=1 << 26)
+        r.set_active(torch.ones(n, dtype=torch.uint8, device=dev), stream=stream)
+        # thresholds: the 99th percentile of each group's nonzero norms after one update pass
+        inf = [float("inf")] * 6
+        _, _, scratch = r.update_active_set(sp, cams, targets, inf, S, int(rng.integers(V)), stream=stream)
+        _, norms = activeness(scratch, inf, stream=stream, with_norms=True)
+        nz = norms[norms.max(dim=1).values > 0]
+        eps = [float(torch.quantile(nz[:, k], 0.99).item()) for k in range(6)]
+        mask = torch.empty(n, dtype=torch.uint8, device=dev)
+        for _ in range(args.warmup):
+            r.update_active_set(sp, cams, targets, eps, S, int(rng.integers(V)), stream=stream, scratch=scratch,
+                                mask=mask)
+        stream.synchronize()
+        times, fracs = [], []
+        with ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_active_update.csv")) as clk:
+            for _ in range(args.steps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                first = int(rng.integers(V))
+                a.record(stream)
+                r.update_active_set(sp, cams, targets, eps, S, first, stream=stream, scratch=scratch, mask=mask)
+                b.record(stream)
+                stream.synchronize()
+                times.append(a.elapsed_time(b))
+                fracs.append(r.n_active / n)
+        clocks = clk.summary()
+        r.close()
+    ms = float(np.mean(times))
+    line = {"metric": "ms per periodic active-set update (30 of 60 views, full-set fwd+bwd, Eq. 8), 1M splats",
+            "value": ms, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "active-set update: unbounded scene, 1M splats, 60 views 1297x840, 30 picked by "
+                                   "farthest point sampling, fused L1, thresholds = 99th percentile of each group's "
+                                   "nonzero norms", "l2": "inputs (60 x 13 MB targets, 300 MB gradients) exceed L2"},
+            "ms_per_subsampled_view": ms / S, "active_fraction_after": float(np.mean(fracs)), "eps": eps,
+            "amortised_ms_per_iteration_at_interval_500": ms / 500.0, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def _err_stats(gpu, ref):
     d = np.abs(gpu - ref)
     return {"max_rel": float(d.max() / max(np.abs(ref).max(), 1e-30)),
@@ -537,7 +595,7 @@ def main():
     ap.add_argument("--proj-lanes", type=int, default=0, help="projection lanes per splat (4, 16; 0 = default)")
     ap.add_argument("--bwd-group", type=int, default=0, help="backward grouping by centre cell (1 on, -1 off, 0 default)")
     ap.add_argument("--tile-order", type=int, default=0, help="rasters take tiles heaviest first (1 on, -1 off, 0 default)")
-    ap.add_argument("--workload", default="unbounded", choices=["unbounded", "batched", "precision"],
+    ap.add_argument("--workload", default="unbounded", choices=["unbounded", "batched", "precision", "active_update"],
                     help="unbounded (default line): 1M splats, one view; batched: 3M splats, 16 views; "
                          "precision: 3M splats, 8 views, BF16 vs FP32 SH")
     args = ap.parse_args()
@@ -551,6 +609,9 @@ def main():
         return
     if args.workload == "precision":
         run_precision(args)
+        return
+    if args.workload == "active_update":
+        run_active_update(args)
         return
 
     import torch

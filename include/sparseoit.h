@@ -262,6 +262,81 @@ const char *sparseoit_last_error(const sparseoit_ctx *ctx);
 /* SPARSEOIT_ABI_VERSION of the loaded library. */
 int sparseoit_version(void);
 
+/* Sec. 4.1, "Updating Active Set via Subsampling" (Alg. 1, the
+ * IsActiveUpdateIteration branch): farthest point sampling of s of the n
+ * training views by camera centre c = -R^T t.  cams: host [n]; first: the
+ * randomly drawn starting view (the caller draws it and passes it in);
+ * out: host int32 [s].  out[0] = first; each next entry is the view whose
+ * (double precision) distance to the nearest view chosen so far is largest
+ * (ties: lowest index).  Host only, no device work; 1 <= s <= n and
+ * 0 <= first < n, else SPARSEOIT_ERR_INVALID_ARG. */
+int sparseoit_fps_views(const sparseoit_camera *cams, int32_t n, int32_t s, int32_t first, int32_t *out);
+
+/* Eq. 8, read as "active if at least one attribute is active" (the text
+ * after Eq. 8): per splat i < n, the Euclidean norms of the gradient of
+ * each attribute group -- mu (3), q (4), log s (3), opacity logit (1),
+ * colour SH h (48), weight SH w (16) -- and d_mask[i] = 1 if some group's
+ * norm exceeds its threshold eps[k] (host float[6], that order), else 0.
+ * g: gradients in full rows indexed by splat (the rows_by_splat layout of
+ * sparseoit_backward; device pointers, FP32; g->sigma is not read);
+ * d_mask: device u8[n]; d_norms: device float [n,6] receiving the norms,
+ * or NULL.  The norms are summed in FP32 in a fixed order.  Asynchronous
+ * on `stream`. */
+int sparseoit_activeness(const sparseoit_grads *g, int64_t n, const float *eps, uint8_t *d_mask, float *d_norms,
+                         void *stream);
+
+/* The whole periodic active-set update of Alg. 1 on the context: picks
+ * n_sub of the n_views training views by sparseoit_fps_views (from
+ * `first`), makes every splat active, and for each picked view j commits
+ * its (empty) complement, renders the full set with the fused L1 loss
+ * against d_targets[j] (device FP32 [H_j, W_j, 3]) and back-propagates,
+ * summing the gradients of the n_sub view losses into `scratch` (full rows
+ * indexed by splat, device FP32, overwritten; scratch->sigma receives the
+ * summed dL/dsigma).  Then sparseoit_activeness(scratch, eps) writes the new
+ * mask to d_mask (device u8[max_splats]) and the call ends with
+ * sparseoit_set_active(d_mask): every view's frozen sums are stale
+ * afterwards and are recommitted when next used (the delayed update of
+ * Sec. 4.1).  cams: host [n_views], the context's views in order (view k
+ * has the context's size k); sel_out: host int32 [n_sub] (nullable)
+ * receives the picked views.  Synchronises `stream` (set_active does). */
+int sparseoit_update_active_set(sparseoit_ctx *ctx, const sparseoit_splats *splats, const sparseoit_camera *cams,
+                                int32_t n_views, const float *const *d_targets, int32_t n_sub, int32_t first,
+                                const float *eps, sparseoit_grads *scratch, uint8_t *d_mask, int32_t *sel_out,
+                                void *stream);
+
+/* A set of FP32 per-splat row arrays (parameters or Adam moments), device
+ * pointers, rows indexed by splat: means [N,3], quats [N,4], log_scales
+ * [N,3], opacity_logits [N], sh_color [N,16,3], sh_weight [N,16], and the
+ * scene scalar sigma [1]. */
+typedef struct {
+    float *means, *quats, *log_scales, *opacity_logits, *sh_color, *sh_weight;
+    float *sigma;
+} sparseoit_rows;
+
+/* Adam hyper-parameters (Sec. 5.1 "Implementation Details": Adam; learning
+ * rates of o, sigma and v from the paper, the rest the caller's). */
+typedef struct {
+    float lr[8];      /* means, quats, log_scales, opacity_logits, sh_color degree 0, sh_color degrees 1-3,
+                         sh_weight, sigma */
+    float beta1, beta2, eps;
+    int32_t step;     /* t >= 1: the bias corrections are 1 - beta^t */
+} sparseoit_adam;
+
+/* Sparse Adam over the active set: for every active splat (the context's
+ * active index list, in its order) and every parameter element,
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *   p -= (lr / (1 - b1^t)) m / (sqrt(v) / sqrt(1 - b2^t) + eps)
+ * (the torch.optim.Adam step).  grads: the compact rows of the last
+ * sparseoit_backward (rows_by_splat = 0, N_A rows in active order; grads->sigma
+ * = dL/dsigma); params, m, v: full rows indexed by splat, updated in place;
+ * rows of inactive splats are neither read nor written.  sigma (params,
+ * m, v ->sigma, all non-null or all null) is updated with lr[7].  The
+ * caller copies the new sigma into sparseoit_splats.sigma (a host value)
+ * before the next forward, and recommits the frozen sums if it changed.
+ * Asynchronous on `stream`. */
+int sparseoit_adam_step(sparseoit_ctx *ctx, const sparseoit_grads *grads, sparseoit_rows *params, sparseoit_rows *m,
+                        sparseoit_rows *v, const sparseoit_adam *cfg, void *stream);
+
 /* Allocation-free active-index compaction.  The paper has no counterpart:
  * this entry point serves callers that cannot allocate device memory --
  * code that must not trigger the device-wide synchronisation that

@@ -16,3 +16,5 @@ from .core import (  # noqa: F401
     render_sums,
     sh_basis,
 )
+from . import active_set  # noqa: F401
+from . import adam  # noqa: F401

@@ -34,9 +34,21 @@ EXPORTED = (
     "sparseoit_commit_frozen", "sparseoit_get_frozen", "sparseoit_forward", "sparseoit_backward",
     "sparseoit_reserve_pairs", "sparseoit_status", "sparseoit_last_counts", "sparseoit_set_counting",
     "sparseoit_set_profiling", "sparseoit_get_profile", "sparseoit_last_error", "sparseoit_version",
-    "sparseoit_compact_active_static", "sparseoit_autotune",
+    "sparseoit_compact_active_static", "sparseoit_autotune", "sparseoit_fps_views", "sparseoit_activeness",
+    "sparseoit_update_active_set", "sparseoit_adam_step",
 )
 STATIC_MAX_SPLATS = 16 * 1024 * 1024
+
+
+class Rows(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("quats", ctypes.c_void_p), ("log_scales", ctypes.c_void_p),
+                ("opacity_logits", ctypes.c_void_p), ("sh_color", ctypes.c_void_p), ("sh_weight", ctypes.c_void_p),
+                ("sigma", ctypes.c_void_p)]
+
+
+class Adam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float * 8), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("step", ctypes.c_int32)]
 
 
 class Camera(ctypes.Structure):
@@ -109,6 +121,11 @@ def load(path: str = LIB_PATH):
             "sparseoit_compact_active_static": ([vp, i64, vp, vp, vp], ctypes.c_int),
             "sparseoit_autotune": ([vp, P(Splats), P(Camera), P(i32), i32, P(vp), P(vp), vp, i32, P(Tuning), vp],
                                    ctypes.c_int),
+            "sparseoit_fps_views": ([P(Camera), i32, i32, i32, P(i32)], ctypes.c_int),
+            "sparseoit_update_active_set": ([vp, P(Splats), P(Camera), i32, P(vp), i32, i32, P(ctypes.c_float),
+                                             P(Grads), vp, P(i32), vp], ctypes.c_int),
+            "sparseoit_adam_step": ([vp, P(Grads), P(Rows), P(Rows), P(Rows), P(Adam), vp], ctypes.c_int),
+            "sparseoit_activeness": ([P(Grads), i64, P(ctypes.c_float), vp, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -55,6 +56,8 @@ struct sparseoit_ctx {
     int64_t *d_npairs = nullptr;
     unsigned long long *d_contrib = nullptr;
     bool counting = false;
+    float *d_upd_image = nullptr;  // image and loss of the active-set update's full-set renders
+    float *d_upd_loss = nullptr;
 
     // profiling: events bracketing every launch while enabled
     bool profiling = false;
@@ -335,7 +338,7 @@ int sparseoit_destroy(sparseoit_ctx *ctx) {
     void *bufs[] = {ctx->d_mask[0], ctx->d_mask[1], ctx->d_idx_active, ctx->d_idx_comp, ctx->d_idx_plus,
                     ctx->d_idx_minus, ctx->d_blk, ctx->d_totals, ctx->d_rec, ctx->d_ext, ctx->d_tile_count,
                     ctx->d_offsets, ctx->d_cursor, ctx->d_order, ctx->d_pairs, ctx->d_sgrad, ctx->d_status, ctx->d_npairs,
-                    ctx->d_contrib};
+                    ctx->d_contrib, ctx->d_upd_image, ctx->d_upd_loss};
     for (void *p : bufs) if (p) cudaFree(p);
     if (ctx->h_totals) cudaFreeHost(ctx->h_totals);
     for (auto &m : ctx->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
@@ -535,6 +538,106 @@ int sparseoit_backward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const
                            ctx->last_n_list, ctx->d_sgrad, g, st);
     }
     CK_LAUNCH("project_bwd_kernel");
+    return SPARSEOIT_OK;
+}
+
+int sparseoit_update_active_set(sparseoit_ctx *ctx, const sparseoit_splats *splats, const sparseoit_camera *cams,
+                                int32_t n_views, const float *const *d_targets, int32_t n_sub, int32_t first,
+                                const float *eps, sparseoit_grads *scratch, uint8_t *d_mask, int32_t *sel_out,
+                                void *stream) {
+    if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
+    if (!splats || !cams || !d_targets || !eps || !scratch || !d_mask)
+        return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "update_active_set: null argument");
+    if (n_views != ctx->n_views) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "update_active_set: need every view");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> sel(n_sub > 0 ? n_sub : 1);
+    int rc = sparseoit_fps_views(cams, n_views, n_sub, first, sel.data());
+    if (rc) return fail(ctx, rc, "update_active_set: bad view subsample (n_sub, first)");
+    for (int k = 0; k < n_sub; ++k)
+        if (!d_targets[sel[k]]) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "update_active_set: null target");
+    if (!ctx->d_upd_image) {
+        CK(cudaMalloc((void **)&ctx->d_upd_image, (size_t)(3 * ctx->max_pix) * sizeof(float)), "cudaMalloc(update image)");
+        CK(cudaMalloc((void **)&ctx->d_upd_loss, sizeof(float)), "cudaMalloc(update loss)");
+    }
+    // every splat active: the full-set render of Alg. 1 (the complement is empty)
+    CK(cudaMemsetAsync(d_mask, 1, (size_t)ctx->N, st), "memset(mask)");
+    rc = sparseoit_set_active(ctx, d_mask, ctx->N, stream);
+    if (rc) return rc;
+    sparseoit_grads g = *scratch;
+    g.rows_by_splat = 1;
+    for (int k = 0; k < n_sub; ++k) {
+        const int32_t j = sel[k];
+        rc = sparseoit_commit_frozen(ctx, splats, &cams[j], j, SPARSEOIT_COMMIT_RECOMPUTE, stream);
+        if (rc) return rc;
+        float *img = ctx->d_upd_image;
+        rc = sparseoit_forward(ctx, splats, &cams[j], &j, 1, &img, &d_targets[j], ctx->d_upd_loss, stream);
+        if (rc) return rc;
+        g.accumulate = k > 0 ? 1 : 0;  // the gradient of the sum of the subsampled views' losses
+        rc = sparseoit_backward(ctx, splats, nullptr, &g, stream);
+        if (rc) return rc;
+    }
+    rc = sparseoit_activeness(&g, ctx->N, eps, d_mask, nullptr, stream);
+    if (rc) return fail(ctx, rc, "update_active_set: activeness launch failed");
+    rc = sparseoit_set_active(ctx, d_mask, ctx->N, stream);
+    if (rc) return rc;
+    if (sel_out)
+        for (int k = 0; k < n_sub; ++k) sel_out[k] = sel[k];
+    return SPARSEOIT_OK;
+}
+
+int sparseoit_adam_step(sparseoit_ctx *ctx, const sparseoit_grads *grads, sparseoit_rows *params, sparseoit_rows *m,
+                        sparseoit_rows *v, const sparseoit_adam *cfg, void *stream) {
+    if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
+    if (!grads || !params || !m || !v || !cfg) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "adam: null argument");
+    if (!ctx->have_mask) return fail(ctx, SPARSEOIT_ERR_STATE, "adam before set_active");
+    if (cfg->step < 1 || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) || !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) ||
+        !(cfg->eps > 0.f))
+        return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "adam: need step >= 1, 0 <= beta < 1, eps > 0");
+    const float *g6[6] = {grads->means, grads->quats, grads->log_scales, grads->opacity_logits, grads->sh_color,
+                          grads->sh_weight};
+    sparseoit_rows *sets[3] = {params, m, v};
+    soit::AdamArgs a;
+    memset(&a, 0, sizeof(a));
+    const int width[6] = {3, 4, 3, 1, 48, 16};
+    for (int k = 0; k < 6; ++k) {
+        float *row[3];
+        for (int j = 0; j < 3; ++j) {
+            sparseoit_rows *r = sets[j];
+            float *q[6] = {r->means, r->quats, r->log_scales, r->opacity_logits, r->sh_color, r->sh_weight};
+            row[j] = q[k];
+        }
+        if ((!g6[k] && ctx->n_active > 0) || !row[0] || !row[1] || !row[2])
+            return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "adam: null array");
+        a.g[k] = g6[k];
+        a.p[k] = row[0];
+        a.m[k] = row[1];
+        a.v[k] = row[2];
+        a.width[k] = width[k];
+    }
+    const bool sig = params->sigma || m->sigma || v->sigma;
+    if (sig && !(params->sigma && m->sigma && v->sigma && grads->sigma))
+        return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "adam: sigma pointers must be all given or all null");
+    const double bc1 = 1.0 - std::pow((double)cfg->beta1, (double)cfg->step);
+    const double bc2 = 1.0 - std::pow((double)cfg->beta2, (double)cfg->step);
+    for (int j = 0; j < 8; ++j) a.step_size[j] = (float)(cfg->lr[j] / bc1);
+    a.inv_sqrt_bc2 = (float)(1.0 / std::sqrt(bc2));
+    a.beta1 = cfg->beta1;
+    a.beta2 = cfg->beta2;
+    a.eps = cfg->eps;
+    a.idx = ctx->d_idx_active;
+    a.n_active = ctx->n_active;
+    if (sig) {
+        a.sigma_g = grads->sigma;
+        a.sigma_p = params->sigma;
+        a.sigma_m = m->sigma;
+        a.sigma_v = v->sigma;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    {
+        ProfScope ps(ctx, "adam", st);
+        soit::launch_adam(a, st);
+    }
+    CK_LAUNCH("adam_kernel");
     return SPARSEOIT_OK;
 }
 

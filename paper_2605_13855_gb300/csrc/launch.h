@@ -37,4 +37,20 @@ int launch_compact(const uint8_t *mask_new, const uint8_t *mask_prev, int64_t n,
                    cudaStream_t st);
 int64_t compact_scratch_ints(int64_t n);
 
+// Sparse Adam (adam.cu): group k = means, quats, log_scales, opacity, sh_color, sh_weight
+// (blockIdx.y); step_size[j] = lr_j / (1 - beta1^t) for the 8 rate classes of sparseoit_adam.
+struct AdamArgs {
+    const int *idx;               // active index list [n_active]
+    int64_t n_active;
+    const float *g[6];            // compact gradient rows
+    float *p[6], *m[6], *v[6];    // full rows by splat
+    int width[6];
+    float step_size[8];
+    float inv_sqrt_bc2;           // 1 / sqrt(1 - beta2^t)
+    float beta1, beta2, eps;
+    const float *sigma_g;
+    float *sigma_p, *sigma_m, *sigma_v;  // null: sigma not updated
+};
+int launch_adam(const AdamArgs &a, cudaStream_t st);
+
 }  // namespace soit

@@ -276,6 +276,76 @@ class Renderer:
         return {"fwd_pixels_per_thread": int(t.fwd_pixels_per_thread),
                 "ms": {int(t.candidates[k]): float(t.ms[k]) for k in range(t.n_candidates)}}
 
+    def update_active_set(self, splats: SplatParams, cams: Sequence[dict], targets: Sequence[torch.Tensor],
+                          eps: Sequence[float], n_sub: int, first: int, stream=None,
+                          scratch: Optional[Dict[str, torch.Tensor]] = None, mask: Optional[torch.Tensor] = None):
+        """The periodic active-set update (Sec. 4.1, Eq. 8; sparseoit_update_active_set).
+
+        cams / targets: every training view of the context, in order.  Returns
+        (mask u8 [N] on the device, picked views list, summed full-row gradients dict)."""
+        nv = len(cams)
+        if nv != len(self.view_sizes) or len(targets) != nv:
+            raise ValueError("need one camera and one target per view of the renderer")
+        s = splats_struct(splats)
+        camarr = (_lib.Camera * nv)(*[camera_struct(c) for c in cams])
+        for tg, (W, H) in zip(targets, self.view_sizes):
+            if tuple(tg.shape) != (H, W, 3) or tg.dtype != torch.float32 or not tg.is_cuda or not tg.is_contiguous():
+                raise ValueError("targets must be contiguous float32 CUDA [H, W, 3]")
+        tptr = (ctypes.c_void_p * nv)(*[tg.data_ptr() for tg in targets])
+        if scratch is None:
+            scratch = {name: torch.empty((self.n,) + PARAM_SHAPES[name], dtype=torch.float32, device="cuda")
+                       for name in PARAM_NAMES}
+            scratch["sigma"] = torch.empty(1, dtype=torch.float32, device="cuda")
+        g = _lib.Grads()
+        for name in PARAM_NAMES + ("sigma",):
+            setattr(g, name, scratch[name].data_ptr())
+        if mask is None:
+            mask = torch.empty(self.n, dtype=torch.uint8, device="cuda")
+        epsa = (ctypes.c_float * 6)(*[float(e) for e in eps])
+        sel = (ctypes.c_int32 * max(1, int(n_sub)))()
+        self._check(self.lib.sparseoit_update_active_set(self._ctx, ctypes.byref(s), camarr, nv, tptr, int(n_sub),
+                                                         int(first), epsa, ctypes.byref(g),
+                                                         ctypes.c_void_p(mask.data_ptr()), sel,
+                                                         ctypes.c_void_p(_stream_ptr(stream))))
+        # the call ends with set_active on the new mask
+        idx, na = ctypes.c_void_p(), ctypes.c_int64()
+        self._check(self.lib.sparseoit_get_active(self._ctx, ctypes.byref(idx), ctypes.byref(na)))
+        self.n_active = int(na.value)
+        self.forward_id += 1
+        return mask, [int(sel[k]) for k in range(int(n_sub))], scratch
+
+    def adam_step(self, grads: Dict[str, torch.Tensor], params: Dict[str, torch.Tensor], m: Dict[str, torch.Tensor],
+                  v: Dict[str, torch.Tensor], lr: Sequence[float], step: int, beta1: float = 0.9,
+                  beta2: float = 0.999, eps: float = 1e-15, stream=None):
+        """Sparse Adam over the active rows (sparseoit_adam_step), in place on params / m / v.
+
+        grads: compact rows of the last backward (active order); params, m, v: full rows by splat
+        (dicts of FP32 CUDA tensors with the parameter names, plus optional "sigma" [1] in all four).
+        lr: 8 rates (means, quats, log_scales, opacity, SH colour degree 0, degrees 1-3, SH weight, sigma)."""
+        def rows(d):
+            r = _lib.Rows()
+            for name in PARAM_NAMES:
+                t = d[name]
+                if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.shape[0] != self.n:
+                    raise ValueError(f"{name} must be contiguous float32 CUDA with {self.n} rows")
+                setattr(r, name, t.data_ptr())
+            r.sigma = d["sigma"].data_ptr() if "sigma" in d else 0
+            return r
+        g = _lib.Grads()
+        for name in PARAM_NAMES:
+            setattr(g, name, grads[name].data_ptr())
+        g.sigma = grads["sigma"].data_ptr() if "sigma" in grads else 0
+        rp, rm, rv = rows(params), rows(m), rows(v)
+        cfg = _lib.Adam()
+        if len(lr) != 8:
+            raise ValueError("need 8 learning rates")
+        for k in range(8):
+            cfg.lr[k] = float(lr[k])
+        cfg.beta1, cfg.beta2, cfg.eps, cfg.step = float(beta1), float(beta2), float(eps), int(step)
+        self._check(self.lib.sparseoit_adam_step(self._ctx, ctypes.byref(g), ctypes.byref(rp), ctypes.byref(rm),
+                                                 ctypes.byref(rv), ctypes.byref(cfg),
+                                                 ctypes.c_void_p(_stream_ptr(stream))))
+
     # ------------------------------------------------------------ misc
     def status(self, stream=None):
         self._check(self.lib.sparseoit_status(self._ctx, ctypes.c_void_p(_stream_ptr(stream))))
@@ -330,3 +400,36 @@ class SparseOITRender(torch.autograd.Function):
         sh_dt = ctx.splats.sh_color.dtype
         return (None, None, None, None, None, grads["means"], grads["quats"], grads["log_scales"],
                 grads["opacity_logits"], grads["sh_color"].to(sh_dt), grads["sh_weight"].to(sh_dt))
+
+
+def fps_views(cams: Sequence[dict], n_sub: int, first: int) -> List[int]:
+    """Farthest point sampling of training views by camera centre (sparseoit_fps_views; host only)."""
+    lib = _lib.load()
+    n = len(cams)
+    camarr = (_lib.Camera * n)(*[camera_struct(c) for c in cams])
+    out = (ctypes.c_int32 * max(1, int(n_sub)))()
+    rc = lib.sparseoit_fps_views(camarr, n, int(n_sub), int(first), out)
+    if rc != _lib.OK:
+        raise SparseOITError(rc, "fps_views: need 1 <= n_sub <= len(cams) and 0 <= first < len(cams)")
+    return [int(out[k]) for k in range(int(n_sub))]
+
+
+def activeness(grads: Dict[str, torch.Tensor], eps: Sequence[float], stream=None, with_norms: bool = False):
+    """Eq. 8 on full gradient rows (sparseoit_activeness): (mask u8 [N], norms [N, 6] or None)."""
+    lib = _lib.load()
+    n = grads["means"].shape[0]
+    g = _lib.Grads()
+    for name in PARAM_NAMES:
+        t = grads[name]
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.shape[0] != n:
+            raise ValueError(f"gradient {name} must be contiguous float32 CUDA with {n} rows")
+        setattr(g, name, t.data_ptr())
+    mask = torch.empty(n, dtype=torch.uint8, device="cuda")
+    norms = torch.empty((n, 6), dtype=torch.float32, device="cuda") if with_norms else None
+    epsa = (ctypes.c_float * 6)(*[float(e) for e in eps])
+    rc = lib.sparseoit_activeness(ctypes.byref(g), n, epsa, ctypes.c_void_p(mask.data_ptr()),
+                                  ctypes.c_void_p(norms.data_ptr() if norms is not None else 0),
+                                  ctypes.c_void_p(_stream_ptr(stream)))
+    if rc != _lib.OK:
+        raise SparseOITError(rc, "activeness launch failed")
+    return mask, norms

@@ -176,6 +176,9 @@ BATCHED = dict(n=3_000_000, seed=4000, active=0.05,
                resolutions=((640, 480), (800, 800), (1297, 840), (1600, 1064)), views_per_res=4)
 PRECISION = dict(n=3_000_000, seed=5000, active=0.05, width=1297, height=840, views=8,
                  crop=(520, 292, 776, 548))
+# periodic active-set update: the unbounded scene seen from 60 training views, 30 picked by
+# farthest point sampling from a seeded first view (the paper's S = 30)
+ACTIVE_UPDATE = dict(n=1_000_000, seed=3000, width=1297, height=840, views=60, n_sub=30, camera_seed=6000)
 
 
 def tiny_workload():
@@ -223,3 +226,8 @@ def batched_cameras(seed: int = BATCHED["seed"]):
 def precision_cameras(seed: int = PRECISION["seed"]):
     return [random_camera(seed + 3 + 17 * k, PRECISION["width"], PRECISION["height"])
             for k in range(PRECISION["views"])]
+
+
+def training_cameras(n_views: int, seed: int, width: int, height: int) -> list:
+    """n_views cameras drawn by the common camera rule, one seed each."""
+    return [random_camera(seed + k, width, height) for k in range(n_views)]

@@ -58,6 +58,7 @@ PROBE = r"""
 int main(void) {
   printf("camera %zu\nsplats %zu\ngrads %zu\nconfig %zu\nktime %zu\n", sizeof(sparseoit_camera),
          sizeof(sparseoit_splats), sizeof(sparseoit_grads), sizeof(sparseoit_config), sizeof(sparseoit_kernel_time));
+  printf("rows %zu\nadam %zu\n", sizeof(sparseoit_rows), sizeof(sparseoit_adam));
   F(sparseoit_camera, fx) F(sparseoit_camera, width) F(sparseoit_camera, height)
   F(sparseoit_splats, sh_color) F(sparseoit_splats, sh_dtype) F(sparseoit_splats, sigma) F(sparseoit_splats, bg)
   F(sparseoit_splats, n)
@@ -67,6 +68,8 @@ int main(void) {
   F(sparseoit_config, reserved)
   F(sparseoit_kernel_time, launches) F(sparseoit_kernel_time, total_ms)
   F(sparseoit_tuning, n_candidates) F(sparseoit_tuning, candidates) F(sparseoit_tuning, ms)
+  F(sparseoit_rows, sh_weight) F(sparseoit_rows, sigma)
+  F(sparseoit_adam, beta1) F(sparseoit_adam, eps) F(sparseoit_adam, step)
   return 0;
 }
 """
@@ -85,9 +88,11 @@ def test_ctypes_structs_match_header(tmp_path):
     assert got["grads"] == ctypes.sizeof(_lib.Grads)
     assert got["config"] == ctypes.sizeof(_lib.Config)
     assert got["ktime"] == ctypes.sizeof(_lib.KernelTime)
+    assert got["rows"] == ctypes.sizeof(_lib.Rows)
+    assert got["adam"] == ctypes.sizeof(_lib.Adam)
     pairs = {"sparseoit_camera": _lib.Camera, "sparseoit_splats": _lib.Splats, "sparseoit_grads": _lib.Grads,
              "sparseoit_config": _lib.Config, "sparseoit_kernel_time": _lib.KernelTime,
-             "sparseoit_tuning": _lib.Tuning}
+             "sparseoit_tuning": _lib.Tuning, "sparseoit_rows": _lib.Rows, "sparseoit_adam": _lib.Adam}
     for key, off in got.items():
         if "." not in key:
             continue
