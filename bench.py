@@ -462,6 +462,63 @@ def run_active_update(args):
     print(json.dumps(line), flush=True)
 
 
+def run_bwd_ablation(args):
+    """Backward ablation (the paper's Tab. 2 analogue) on the headline workload: the step and the
+    backward raster with per-splat lanes (this library's design), per-pixel threads with warp-reduced
+    atomics, and per-pixel threads with one set of atomics per contributing pair (the 3DGS scheme)."""
+    import torch
+    import __graft_entry__
+    from paper_2605_13855_gb300 import scenes
+    from paper_2605_13855_gb300.renderer import Renderer, SplatParams
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    c = scenes.UNBOUNDED
+    scene, cam, target_np = scenes.unbounded_workload()
+    n, W, H = c["n"], c["width"], c["height"]
+    sp = SplatParams.from_numpy(scene, device=dev)
+    target = torch.as_tensor(target_np, device=dev)
+    img = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {}
+    for frac in (0.05, 1.0):
+        mask = torch.as_tensor(scenes.unbounded_active_mask(scene, frac), device=dev)
+        for mode, name in ((1, "per_splat"), (2, "per_pixel_warp_reduced"), (3, "per_pixel_atomics")):
+            with torch.cuda.stream(stream):
+                r = Renderer(n, [(W, H)], max_pairs=1 << 26, bwd_parallel=mode)
+                r.set_active(mask, stream=stream)
+                r.commit_frozen(sp, cam, 0, mode="recompute", stream=stream)
+                out = _grad_out(torch, r.n_active, dev)
+
+                def step(r=r, out=out):
+                    r.forward(sp, [cam], [0], targets=[target], stream=stream, images=[img], loss=loss)
+                    r.backward(sp, stream=stream, out=out)
+
+                ms = _graph_time(torch, stream, flush, step, args.steps, args.warmup)
+                r.set_profiling(True)
+                r.get_profile()
+                for _ in range(args.steps):
+                    flush.zero_()
+                    step()
+                stream.synchronize()
+                prof = r.get_profile()
+                r.set_profiling(False)
+                r.status(stream)
+                r.close()
+            bw = prof.get("raster_bwd", (1, 0.0))
+            res[f"{frac}"] = res.get(f"{frac}", {})
+            res[f"{frac}"][name] = {"step_ms": ms, "raster_bwd_ms": bw[1] / max(1, bw[0])}
+    head = res["0.05"]
+    line = {"metric": "backward ablation: ms per fwd+bwd step and backward-raster ms, 1M splats, 1297x840",
+            "value": head["per_pixel_atomics"]["step_ms"] / head["per_splat"]["step_ms"],
+            "unit": "step speedup of per-splat over per-pixel atomics (5% active)", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["per_splat"]["step_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "fractions": [0.05, 1.0]}, "modes": res}
+    print(json.dumps(line), flush=True)
+
+
 def _err_stats(gpu, ref):
     d = np.abs(gpu - ref)
     return {"max_rel": float(d.max() / max(np.abs(ref).max(), 1e-30)),
@@ -595,7 +652,8 @@ def main():
     ap.add_argument("--proj-lanes", type=int, default=0, help="projection lanes per splat (4, 16; 0 = default)")
     ap.add_argument("--bwd-group", type=int, default=0, help="backward grouping by centre cell (1 on, -1 off, 0 default)")
     ap.add_argument("--tile-order", type=int, default=0, help="rasters take tiles heaviest first (1 on, -1 off, 0 default)")
-    ap.add_argument("--workload", default="unbounded", choices=["unbounded", "batched", "precision", "active_update"],
+    ap.add_argument("--workload", default="unbounded", choices=["unbounded", "batched", "precision", "active_update",
+                                                                  "bwd_ablation"],
                     help="unbounded (default line): 1M splats, one view; batched: 3M splats, 16 views; "
                          "precision: 3M splats, 8 views, BF16 vs FP32 SH")
     args = ap.parse_args()
@@ -612,6 +670,9 @@ def main():
         return
     if args.workload == "active_update":
         run_active_update(args)
+        return
+    if args.workload == "bwd_ablation":
+        run_bwd_ablation(args)
         return
 
     import torch
@@ -743,6 +804,7 @@ def main():
 
     set_active_ms = commit_inc_ms = None
     e2e_ms, h2d, d2h = None, 0, 0
+    train = dssim = None
     if not args.no_e2e:
         # active-set update (compaction of a changed mask) and the delayed,
         # incremental frozen-sum update it implies
@@ -800,6 +862,63 @@ def main():
         if ws > 1:
             e2e_ms, _ = reduce_over_ranks(e2e_ms, 0.0, device=dev)
 
+        # a whole training iteration of the active-set loop: the step plus the sparse Adam update
+        # of the active rows (in place on copies of the parameters, moments by splat)
+        from paper_2605_13855_gb300.renderer import PARAM_NAMES, SplatParams
+        spt = SplatParams(*[getattr(sp, k).clone() for k in PARAM_NAMES], sp.sigma, sp.bg)
+        P = {k: getattr(spt, k) for k in PARAM_NAMES}
+        P["sigma"] = torch.tensor([sp.sigma], dtype=torch.float32, device=dev)
+        Mo = {k: torch.zeros_like(v) for k, v in P.items()}
+        Vo = {k: torch.zeros_like(v) for k, v in P.items()}
+        lr = [1.6e-4, 1e-3, 5e-3, 1e-2, 2.5e-3, 1.25e-4, 5e-3, 0.1]
+        with torch.cuda.stream(stream):
+            r.set_active(make(HEADLINE_FRACTION), stream=stream)
+            r.commit_frozen(spt, cam, 0, mode="recompute", stream=stream)
+            out = grads_for(r.n_active)
+
+        def train_step():
+            r.forward(spt, [cam], [0], targets=[target], stream=stream, images=[img], loss=loss)
+            r.backward(spt, stream=stream, out=out)
+            r.adam_step(out, P, Mo, Vo, lr, 100, stream=stream)
+
+        train_ms = _graph_time(torch, stream, flush, train_step, args.steps, args.warmup)
+        with torch.cuda.stream(stream):
+            r.set_profiling(True)
+            r.get_profile()
+            for _ in range(args.steps):
+                flush.zero_()
+                r.adam_step(out, P, Mo, Vo, lr, 100, stream=stream)
+            stream.synchronize()
+            adam_prof = r.get_profile().get("adam", (1, 0.0))
+            r.set_profiling(False)
+        adam_ms = adam_prof[1] / max(1, adam_prof[0])
+        adam_bytes = r.n_active * (4 + 300 + 3 * 600)  # index, compact grads, (p, m, v) read + write
+        # the same step with the 3DGS loss (0.8 L1 + 0.2 D-SSIM) instead of the fused L1
+        def dssim_step():
+            r.forward(spt, [cam], [0], stream=stream, images=[img])
+            r.loss_l1_dssim([target], 0.2, stream=stream, loss=loss)
+            r.backward(spt, stream=stream, out=out)
+
+        dssim_ms = _graph_time(torch, stream, flush, dssim_step, args.steps, args.warmup)
+        with torch.cuda.stream(stream):
+            r.set_profiling(True)
+            r.get_profile()
+            for _ in range(args.steps):
+                flush.zero_()
+                dssim_step()
+            stream.synchronize()
+            ssim_prof = r.get_profile().get("ssim", (1, 0.0))
+            r.set_profiling(False)
+        ssim_ms = ssim_prof[1] / max(1, ssim_prof[0])
+        # per pixel: image + target read twice (x, y) = 48 B, 9 maps written and read = 72 B,
+        # (F, T, Q) read and the state written = 40 B
+        ssim_bytes = W * H * (48 + 72 + 40)
+        dssim = {"step_ms": dssim_ms, "ssim_kernels_ms": ssim_ms,
+                 "ssim_gbs": ssim_bytes / (ssim_ms * 1e-3) / 1e9, "ssim_algorithmic_bytes": ssim_bytes}
+        train = {"ms": train_ms, "adam_ms": adam_ms, "adam_gbs": adam_bytes / (adam_ms * 1e-3) / 1e9,
+                 "adam_hbm_frac": adam_bytes / (adam_ms * 1e-3) / 1e9 / float(_peaks()[0].get("hbm_gbs", 6800.0)),
+                 "adam_algorithmic_bytes": adam_bytes}
+
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -852,6 +971,8 @@ def main():
         "stage_update": {"set_active_ms": set_active_ms, "commit_incremental_ms": commit_inc_ms},
         "per_kernel_ms": per_kernel,
         "roofline": roofline,
+        "train_iteration_with_sparse_adam": train,
+        "step_with_l1_dssim_loss": dssim,
         "evals_tile_per_s": 256 * head["M"] / (ms * 1e-3),
         "hbm": hbm,
         "cpu_baseline": cpu,

@@ -130,8 +130,8 @@ typedef struct {
     int32_t fwd_pixels_per_thread; /* forward raster: pixels per thread, 1, 2 or 4
                                       (256 / 128 / 64 threads per 16x16 tile);
                                       0 = default (4)                          */
-    int32_t proj_lanes_per_splat;  /* projection: lanes per splat, 4 or 16;
-                                      0 = default (4)                          */
+    int32_t proj_lanes_per_splat;  /* projection: lanes per splat, 1, 2, 4 or
+                                      16; 0 = default (4)                      */
     int32_t bwd_group_by_cell;     /* backward raster: order each round of a
                                       tile's splats by the 4x4-pixel cell of
                                       their centre before assigning warps;
@@ -140,7 +140,15 @@ typedef struct {
                                       ranked by pair count in four classes per
                                       octave) instead of in index order;
                                       1 = on, -1 = off, 0 = default (on)       */
-    int32_t reserved[2];
+    int32_t bwd_parallel;          /* backward raster organisation (the
+                                      ablation of Sec. 5.3, Tab. 2):
+                                      0 = default = 1; 1 = per splat (a lane
+                                      per splat, pixel states in shared
+                                      memory, one atomic set per splat and
+                                      tile); 2 = per pixel, warp-reduced
+                                      atomics; 3 = per pixel, one atomic set
+                                      per contributing pair (3DGS)          */
+    int32_t reserved[1];
 } sparseoit_config;
 
 /* Create a context for a scene of max_splats splats and n_views training
@@ -303,6 +311,22 @@ int sparseoit_update_active_set(sparseoit_ctx *ctx, const sparseoit_splats *spla
                                 int32_t n_views, const float *const *d_targets, int32_t n_sub, int32_t first,
                                 const float *eps, sparseoit_grads *scratch, uint8_t *d_mask, int32_t *sel_out,
                                 void *stream);
+
+/* The photometric loss of 3DGS, which the paper keeps (Sec. 5.1):
+ * L = sum over the views of the last forward of
+ *     (1 - lambda) mean|C - I| + lambda (1 - SSIM(C, I)),
+ * SSIM per colour channel with an 11 x 11 Gaussian window (sigma 1.5), zero
+ * padding, C1 = 0.01^2, C2 = 0.03^2, averaged over pixels and channels (3DGS
+ * uses lambda = 0.2).  Call it after a sparseoit_forward without targets: it
+ * reads that forward's images, writes *d_loss (device float), optionally the
+ * image gradients dL/dC to d_grad_images[k] (host array of device [H, W, 3]
+ * FP32 pointers, or NULL), and leaves the pixel state so that
+ * sparseoit_backward(..., d_grad_images = NULL, ...) back-propagates L.
+ * d_targets: host array of device [H, W, 3] FP32 pointers, one per view of
+ * the forward; bg: host float[3], the background of that forward.
+ * ERR_STATE if there is no such forward (or its state was already used). */
+int sparseoit_loss_l1_dssim(sparseoit_ctx *ctx, const float *const *d_targets, float lambda, float *d_loss,
+                            float *const *d_grad_images, const float *bg, void *stream);
 
 /* A set of FP32 per-splat row arrays (parameters or Adam moments), device
  * pointers, rows indexed by splat: means [N,3], quats [N,4], log_scales

@@ -18,3 +18,4 @@ from .core import (  # noqa: F401
 )
 from . import active_set  # noqa: F401
 from . import adam  # noqa: F401
+from . import ssim  # noqa: F401

@@ -35,7 +35,7 @@ EXPORTED = (
     "sparseoit_reserve_pairs", "sparseoit_status", "sparseoit_last_counts", "sparseoit_set_counting",
     "sparseoit_set_profiling", "sparseoit_get_profile", "sparseoit_last_error", "sparseoit_version",
     "sparseoit_compact_active_static", "sparseoit_autotune", "sparseoit_fps_views", "sparseoit_activeness",
-    "sparseoit_update_active_set", "sparseoit_adam_step",
+    "sparseoit_update_active_set", "sparseoit_adam_step", "sparseoit_loss_l1_dssim",
 )
 STATIC_MAX_SPLATS = 16 * 1024 * 1024
 
@@ -82,7 +82,8 @@ class Tuning(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("max_pairs", ctypes.c_int64), ("fwd_pixels_per_thread", ctypes.c_int32),
                 ("proj_lanes_per_splat", ctypes.c_int32), ("bwd_group_by_cell", ctypes.c_int32),
-                ("raster_tile_order", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("raster_tile_order", ctypes.c_int32), ("bwd_parallel", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 _lock = threading.Lock()
@@ -124,6 +125,7 @@ def load(path: str = LIB_PATH):
             "sparseoit_fps_views": ([P(Camera), i32, i32, i32, P(i32)], ctypes.c_int),
             "sparseoit_update_active_set": ([vp, P(Splats), P(Camera), i32, P(vp), i32, i32, P(ctypes.c_float),
                                              P(Grads), vp, P(i32), vp], ctypes.c_int),
+            "sparseoit_loss_l1_dssim": ([vp, P(vp), ctypes.c_float, vp, P(vp), P(ctypes.c_float), vp], ctypes.c_int),
             "sparseoit_adam_step": ([vp, P(Grads), P(Rows), P(Rows), P(Rows), P(Adam), vp], ctypes.c_int),
             "sparseoit_activeness": ([P(Grads), i64, P(ctypes.c_float), vp, vp, vp], ctypes.c_int),
         }

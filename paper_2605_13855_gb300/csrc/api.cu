@@ -27,6 +27,7 @@ struct sparseoit_ctx {
     int proj_lanes = 4;           // lanes per splat of the projection
     bool bwd_group = false;       // backward: group a tile's splats by centre cell
     bool tile_order = true;       // rasters take tiles heaviest first
+    int bwd_parallel = 1;         // 1 per splat, 2 per pixel warp-reduced, 3 per pixel per-pair atomics
     std::string err;
 
     // active set
@@ -56,6 +57,8 @@ struct sparseoit_ctx {
     int64_t *d_npairs = nullptr;
     unsigned long long *d_contrib = nullptr;
     bool counting = false;
+    float *d_ssim_abc = nullptr;   // D-SSIM: 9 planes of the largest view
+    double *d_ssim_sums = nullptr; // D-SSIM: 2 sums per view of a batch
     float *d_upd_image = nullptr;  // image and loss of the active-set update's full-set renders
     float *d_upd_loss = nullptr;
 
@@ -279,14 +282,21 @@ int sparseoit_create(sparseoit_ctx **out, int64_t max_splats, int32_t n_views, c
     }
     if (cfg && cfg->proj_lanes_per_splat != 0) {
         const int l = cfg->proj_lanes_per_splat;
-        if (l != 4 && l != 16) {
+        if (l != 1 && l != 2 && l != 4 && l != 16) {
             delete ctx;
-            return fail(nullptr, SPARSEOIT_ERR_INVALID_ARG, "proj_lanes_per_splat must be 4 or 16");
+            return fail(nullptr, SPARSEOIT_ERR_INVALID_ARG, "proj_lanes_per_splat must be 1, 2, 4 or 16");
         }
         ctx->proj_lanes = l;
     }
     if (cfg && cfg->bwd_group_by_cell != 0) ctx->bwd_group = cfg->bwd_group_by_cell > 0;
     if (cfg && cfg->raster_tile_order != 0) ctx->tile_order = cfg->raster_tile_order > 0;
+    if (cfg && cfg->bwd_parallel != 0) {
+        if (cfg->bwd_parallel < 1 || cfg->bwd_parallel > 3) {
+            delete ctx;
+            return fail(nullptr, SPARSEOIT_ERR_INVALID_ARG, "bwd_parallel must be 1, 2 or 3");
+        }
+        ctx->bwd_parallel = cfg->bwd_parallel;
+    }
     if (ctx->pair_cap > 0x7fffffffll) ctx->pair_cap = 0x7fffffffll;
     ctx->view_gen.assign(n_views, -1);
     ctx->d_frozen.assign(n_views, nullptr);
@@ -338,7 +348,7 @@ int sparseoit_destroy(sparseoit_ctx *ctx) {
     void *bufs[] = {ctx->d_mask[0], ctx->d_mask[1], ctx->d_idx_active, ctx->d_idx_comp, ctx->d_idx_plus,
                     ctx->d_idx_minus, ctx->d_blk, ctx->d_totals, ctx->d_rec, ctx->d_ext, ctx->d_tile_count,
                     ctx->d_offsets, ctx->d_cursor, ctx->d_order, ctx->d_pairs, ctx->d_sgrad, ctx->d_status, ctx->d_npairs,
-                    ctx->d_contrib, ctx->d_upd_image, ctx->d_upd_loss};
+                    ctx->d_contrib, ctx->d_upd_image, ctx->d_upd_loss, ctx->d_ssim_abc, ctx->d_ssim_sums};
     for (void *p : bufs) if (p) cudaFree(p);
     if (ctx->h_totals) cudaFreeHost(ctx->h_totals);
     for (auto &m : ctx->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
@@ -524,8 +534,12 @@ int sparseoit_backward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const
     CK(cudaMemsetAsync(ctx->d_sgrad, 0, (size_t)(3 * nrec) * sizeof(float4), st), "memset(screen grads)");
     {
         ProfScope ps(ctx, "raster_bwd", st);
-        launch_raster_bwd(b, ctx->bwd_group, ctx->d_rec, ctx->d_offsets, ctx->d_pairs, ctx->pair_cap, ctx->d_sgrad,
-                          st);
+        if (ctx->bwd_parallel == 1)
+            launch_raster_bwd(b, ctx->bwd_group, ctx->d_rec, ctx->d_offsets, ctx->d_pairs, ctx->pair_cap,
+                              ctx->d_sgrad, st);
+        else
+            launch_raster_bwd_pixel(b, ctx->bwd_parallel == 2, ctx->d_rec, ctx->d_offsets, ctx->d_pairs,
+                                    ctx->pair_cap, ctx->d_sgrad, st);
     }
     CK_LAUNCH("raster_bwd_kernel");
     if (!out->accumulate) CK(cudaMemsetAsync(out->sigma, 0, sizeof(float), st), "memset(dsigma)");
@@ -638,6 +652,50 @@ int sparseoit_adam_step(sparseoit_ctx *ctx, const sparseoit_grads *grads, sparse
         soit::launch_adam(a, st);
     }
     CK_LAUNCH("adam_kernel");
+    return SPARSEOIT_OK;
+}
+
+int sparseoit_loss_l1_dssim(sparseoit_ctx *ctx, const float *const *d_targets, float lambda, float *d_loss,
+                            float *const *d_grad_images, const float *bg, void *stream) {
+    if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
+    if (!d_targets || !d_loss || !bg) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "loss: null argument");
+    if (!(lambda >= 0.f && lambda <= 1.f)) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "loss: lambda outside [0, 1]");
+    if (!ctx->have_fwd || ctx->last_generation != ctx->generation || ctx->last_fused)
+        return fail(ctx, SPARSEOIT_ERR_STATE, "loss: needs the state of a forward run without targets");
+    cudaStream_t st = (cudaStream_t)stream;
+    Batch &b = ctx->last_batch;
+    for (int k = 0; k < b.n_views; ++k)
+        if (!d_targets[k]) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "loss: null target");
+    if (!ctx->d_ssim_abc) {
+        CK(cudaMalloc((void **)&ctx->d_ssim_abc, (size_t)(9 * ctx->max_pix) * sizeof(float)), "cudaMalloc(ssim)");
+        CK(cudaMalloc((void **)&ctx->d_ssim_sums, (size_t)(2 * kMaxViews) * sizeof(double)), "cudaMalloc(ssim sums)");
+    }
+    CK(cudaMemsetAsync(ctx->d_ssim_sums, 0, (size_t)(2 * b.n_views) * sizeof(double), st), "memset(ssim sums)");
+    soit::SsimWindow win;
+    {
+        double g[11], sum = 0.0;
+        for (int k = 0; k < 11; ++k) {
+            const double x = k - 5;
+            g[k] = std::exp(-x * x / (2.0 * 1.5 * 1.5));
+            sum += g[k];
+        }
+        for (int k = 0; k < 11; ++k) win.w[k] = (float)(g[k] / sum);
+    }
+    soit::SsimLossArgs la;
+    memset(&la, 0, sizeof(la));
+    la.n_views = b.n_views;
+    la.lambda = lambda;
+    for (int k = 0; k < b.n_views; ++k) {
+        const ViewDesc &vd = b.v[k];
+        la.inv_n[k] = 1.0 / (3.0 * (double)vd.W * (double)vd.H);
+        ProfScope ps(ctx, "ssim", st);
+        soit::launch_ssim_view(vd.image, d_targets[k], vd.W, vd.H, win, ctx->d_ssim_abc, ctx->d_ssim_sums + 2 * k,
+                               lambda, bg, vd.state, d_grad_images ? d_grad_images[k] : nullptr, st);
+        CK_LAUNCH("ssim kernels");
+    }
+    soit::launch_ssim_loss(ctx->d_ssim_sums, la, d_loss, st);
+    CK_LAUNCH("ssim_loss_kernel");
+    ctx->last_fused = true;  // the state planes now hold the backward state
     return SPARSEOIT_OK;
 }
 

@@ -24,6 +24,11 @@ int launch_prep_state(const Batch &b, const float bg[3], cudaStream_t st);
 int launch_raster_bwd(const Batch &b, bool group, const float4 *rec, const int *offsets, const uint32_t *pairs,
                       int64_t cap, float4 *sgrad, cudaStream_t st);
 
+// Per-pixel backward (raster_bwd_pixel.cu), the ablation baseline: warp_reduce = sum the warp's
+// pixels before the atomics, else one set of atomics per contributing pair.
+int launch_raster_bwd_pixel(const Batch &b, bool warp_reduce, const float4 *rec, const int *offsets,
+                            const uint32_t *pairs, int64_t cap, float4 *sgrad, cudaStream_t st);
+
 struct GradPtrs {
     float *means, *quats, *log_scales, *opacity_logits, *sh_color, *sh_weight, *sigma;
     int rows_by_splat;
@@ -52,5 +57,20 @@ struct AdamArgs {
     float *sigma_p, *sigma_m, *sigma_v;  // null: sigma not updated
 };
 int launch_adam(const AdamArgs &a, cudaStream_t st);
+
+// D-SSIM loss (ssim.cu): the 11-tap Gaussian window, per-view loss constants.
+struct SsimWindow {
+    float w[11];
+};
+struct SsimLossArgs {
+    int n_views;
+    double lambda;
+    double inv_n[kMaxViews];  // 1 / (3 H W) per view
+};
+// One view: abc = 9 planes of H W floats (scratch), sums = 2 doubles (S, |x - y|), state = the view's
+// five planes (F, T, Q in; the backward state out), grad_out = dL/dC [H, W, 3] or null.
+int launch_ssim_view(const float *img, const float *tgt, int W, int H, const SsimWindow &win, float *abc,
+                     double *sums, float lambda, const float bg[3], float *state, float *grad_out, cudaStream_t st);
+int launch_ssim_loss(const double *sums, const SsimLossArgs &a, float *loss, cudaStream_t st);
 
 }  // namespace soit

@@ -159,10 +159,26 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Ba
                 }
             }
         }
-        if (k == 0) rec[3 * qidx + 0] = r0;
-        else if (k == 1) rec[3 * qidx + 1] = r1;
-        else if (k == 2) rec[3 * qidx + 2] = r2;
-        else if (k == 3) ext[qidx] = e;
+        // the four 16-byte outputs, lane k of the group storing outputs k, k + G, ...
+        if (G >= 4) {
+            if (k == 0) rec[3 * qidx + 0] = r0;
+            else if (k == 1) rec[3 * qidx + 1] = r1;
+            else if (k == 2) rec[3 * qidx + 2] = r2;
+            else if (k == 3) ext[qidx] = e;
+        } else if (G == 2) {
+            if (k == 0) {
+                rec[3 * qidx + 0] = r0;
+                rec[3 * qidx + 2] = r2;
+            } else {
+                rec[3 * qidx + 1] = r1;
+                ext[qidx] = e;
+            }
+        } else {
+            rec[3 * qidx + 0] = r0;
+            rec[3 * qidx + 1] = r1;
+            rec[3 * qidx + 2] = r2;
+            ext[qidx] = e;
+        }
     }
 }
 
@@ -332,6 +348,10 @@ int launch_project(const Batch &b, const SplatPtrs &sp, bool bf16, int lanes, co
     if (n1 + n2 == 0) return 0;
     if (lanes == 16)
         launch_project_g<16>(b, sp, bf16, list1, n1, list2, n2, rec, ext, tile_count, st);
+    else if (lanes == 2)
+        launch_project_g<2>(b, sp, bf16, list1, n1, list2, n2, rec, ext, tile_count, st);
+    else if (lanes == 1)
+        launch_project_g<1>(b, sp, bf16, list1, n1, list2, n2, rec, ext, tile_count, st);
     else
         launch_project_g<4>(b, sp, bf16, list1, n1, list2, n2, rec, ext, tile_count, st);
     return 0;

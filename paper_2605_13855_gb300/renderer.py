@@ -113,7 +113,7 @@ class Renderer:
 
     def __init__(self, n_splats: int, view_sizes: Sequence[Sequence[int]], max_pairs: int = 0,
                  fwd_pixels_per_thread: int = 0, proj_lanes_per_splat: int = 0, bwd_group_by_cell: int = 0,
-                 raster_tile_order: int = 0):
+                 raster_tile_order: int = 0, bwd_parallel: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("sparseoit needs a CUDA device")
         self.lib = _lib.load()
@@ -128,6 +128,7 @@ class Renderer:
         cfg.proj_lanes_per_splat = int(proj_lanes_per_splat)
         cfg.bwd_group_by_cell = int(bwd_group_by_cell)
         cfg.raster_tile_order = int(raster_tile_order)
+        cfg.bwd_parallel = int(bwd_parallel)
         self._ctx = ctypes.c_void_p()
         rc = self.lib.sparseoit_create(ctypes.byref(self._ctx), self.n, nv, ws, hs, ctypes.byref(cfg))
         if rc != _lib.OK:
@@ -221,8 +222,33 @@ class Renderer:
                                                ctypes.c_void_p(_stream_ptr(stream))))
         self.forward_id += 1
         self._last_views = list(views)
+        self._last_bg = tuple(float(x) for x in splats.bg)
         self._keep = (images, targets, loss)
         return images, loss
+
+    def loss_l1_dssim(self, targets: Sequence[torch.Tensor], lam: float = 0.2, stream=None,
+                      loss: Optional[torch.Tensor] = None, grad_images: Optional[Sequence[torch.Tensor]] = None):
+        """(1 - lam) L1 + lam (1 - SSIM) of the last forward's images (run without targets) against
+        `targets` (sparseoit_loss_l1_dssim); prepares the backward.  Returns the loss tensor [1]."""
+        views = self._last_views
+        if len(targets) != len(views):
+            raise ValueError("one target per view of the last forward")
+        for tg, v in zip(targets, views):
+            W, H = self.view_sizes[v]
+            if tuple(tg.shape) != (H, W, 3) or tg.dtype != torch.float32 or not tg.is_cuda or not tg.is_contiguous():
+                raise ValueError("targets must be contiguous float32 CUDA [H, W, 3]")
+        nv = len(views)
+        tptr = (ctypes.c_void_p * nv)(*[tg.data_ptr() for tg in targets])
+        gptr = None
+        if grad_images is not None:
+            gptr = (ctypes.c_void_p * nv)(*[g.data_ptr() for g in grad_images])
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        bg = (ctypes.c_float * 3)(*self._last_bg)
+        self._check(self.lib.sparseoit_loss_l1_dssim(self._ctx, tptr, float(lam), ctypes.c_void_p(loss.data_ptr()),
+                                                     gptr, bg, ctypes.c_void_p(_stream_ptr(stream))))
+        self._keep_loss = (targets, grad_images, loss)
+        return loss
 
     def backward(self, splats: SplatParams, grad_images: Optional[Sequence[torch.Tensor]] = None,
                  rows_by_splat: bool = False, stream=None, out: Optional[Dict[str, torch.Tensor]] = None,

@@ -64,7 +64,7 @@ int main(void) {
   F(sparseoit_splats, n)
   F(sparseoit_grads, sigma) F(sparseoit_grads, rows_by_splat) F(sparseoit_grads, accumulate)
   F(sparseoit_config, max_pairs) F(sparseoit_config, fwd_pixels_per_thread)
-  F(sparseoit_config, proj_lanes_per_splat) F(sparseoit_config, bwd_group_by_cell) F(sparseoit_config, raster_tile_order)
+  F(sparseoit_config, proj_lanes_per_splat) F(sparseoit_config, bwd_group_by_cell) F(sparseoit_config, raster_tile_order) F(sparseoit_config, bwd_parallel)
   F(sparseoit_config, reserved)
   F(sparseoit_kernel_time, launches) F(sparseoit_kernel_time, total_ms)
   F(sparseoit_tuning, n_candidates) F(sparseoit_tuning, candidates) F(sparseoit_tuning, ms)
