@@ -31,9 +31,11 @@ namespace soit {
 //   dL/dmu'x = -K A2 Se,  dL/dmu'y = K (A2 r Se - B2^2 Sdy),
 //   dL/dr = -K A2 Sey,    dL/dA2 = K See / A2,  dL/dB2 = K B2 Sdyy.
 // kGroup: before a round of 256 of the tile's splats is split into warps, a
-// shared-memory counting sort orders it by the 4x4-pixel cell of the tile
-// that holds the splat's centre (clamped), so that the 32 splats of a warp
-// tend to cover the same pixels.
+// shared-memory counting sort puts first the splats whose cutoff ellipse
+// contains the whole tile, then the others by the 4x4-pixel cell of the tile
+// that holds their centre (clamped).  A warp whose splats all contain the
+// tile evaluates every pixel without the cutoff test (no divergence); the
+// others tend to share rows and columns.
 //
 // Each lane evaluates two adjacent columns per step with paired FP32
 // instructions (f32x2 FMA / multiply / add, one issue slot for two values);
@@ -41,8 +43,72 @@ namespace soit {
 // fetches a component for both pixels.  Components of the paired operations
 // round exactly like their scalar counterparts, so contribution decisions
 // stay identical to the forward raster's.
+constexpr int kBwdKeys = 18;  // splat classes of the optional per-round ordering
+
+// Per-lane accumulators of one splat over the tile (see the sums above).
+struct BwdAcc {
+    float2 See, gw, gc0, gc1, gc2;
+    float Se, Sey, Sd, Sdy, Sdyy;
+};
+struct BwdSplat {
+    float2 A2p, wp, l2op, c0p, c1p, c2p;
+    float A2dx0, dy0, rA2, B2, thr;
+};
+
+// Rows [rlo, rhi] of the tile for one lane's splat, two adjacent pixels per
+// step.  kTest: test every pixel against the cutoff (the pair contributes iff
+// s <= thr); without it every pixel of the rows contributes (the caller knows
+// the whole tile lies inside the cutoff ellipse).
+template <bool kTest>
+__device__ __forceinline__ void bwd_rows(const BwdSplat &bs, const float2 (*sp)[kTilePix / 2], int rlo, int rhi,
+                                         BwdAcc &acc) {
+    const float2 zero2 = make_float2(0.f, 0.f);
+    const float2 m1 = make_float2(-1.f, -1.f), one2 = make_float2(1.f, 1.f);
+    for (int ky = rlo; ky <= rhi; ++ky) {
+        const RowTerms rt = row_terms(bs.A2dx0, bs.dy0, bs.rA2, bs.B2, ky);
+        const float2 e10p = make_float2(rt.e10, rt.e10), e2p = make_float2(rt.e2sq, rt.e2sq);
+        float2 Rd = zero2, Re = zero2;
+#pragma unroll
+        for (int kp = 0; kp < kTile / 2; ++kp) {
+            const float2 e1 = __ffma2_rn(bs.A2p, make_float2((float)(2 * kp), (float)(2 * kp + 1)), e10p);
+            const float2 sq = __ffma2_rn(e1, e1, e2p);
+            const bool in0 = !kTest || sq.x <= bs.thr, in1 = !kTest || sq.y <= bs.thr;
+            if (in0 || in1) {
+                const int kk = ky * (kTile / 2) + kp;
+                const float2 b0 = sp[0][kk], b1 = sp[1][kk], b2 = sp[2][kk];
+                const float2 Ap = sp[3][kk], nbF = sp[4][kk];
+                // log2 o - s: -s + log2 o rounds once, exactly like the forward's subtraction
+                const float2 lg = __ffma2_rn(sq, m1, bs.l2op);
+                const float ar0 = fast_exp2(lg.x), ar1 = fast_exp2(lg.y);
+                const float2 a = make_float2(in0 ? fminf(ar0, kAlphaMax) : 0.f, in1 ? fminf(ar1, kAlphaMax) : 0.f);
+                // the alpha path (o, mu', conic) is off where alpha is clamped
+                const float2 am = make_float2(ar0 > kAlphaMax ? 0.f : a.x, ar1 > kAlphaMax ? 0.f : a.y);
+                const float2 D = __ffma2_rn(b0, bs.c0p, __ffma2_rn(b1, bs.c1p, __ffma2_rn(b2, bs.c2p, nbF)));
+                const float2 oma = __ffma2_rn(a, m1, one2);  // 1 - a
+                const float2 inv = make_float2(fast_rcp(oma.x), fast_rcp(oma.y));
+                const float2 dLda = __ffma2_rn(Ap, inv, __fmul2_rn(bs.wp, D));
+                acc.gw = __ffma2_rn(a, D, acc.gw);
+                acc.gc0 = __ffma2_rn(a, b0, acc.gc0);  // times w in the epilogue
+                acc.gc1 = __ffma2_rn(a, b1, acc.gc1);
+                acc.gc2 = __ffma2_rn(a, b2, acc.gc2);
+                const float2 da = __fmul2_rn(dLda, am);
+                Rd = __fadd2_rn(Rd, da);
+                const float2 qd = __fmul2_rn(da, e1);
+                Re = __fadd2_rn(Re, qd);
+                acc.See = __ffma2_rn(qd, e1, acc.See);
+            }
+        }
+        const float rd = Rd.x + Rd.y, re = Re.x + Re.y;
+        acc.Sd += rd;
+        acc.Sdy = fmaf(rd, rt.dy, acc.Sdy);
+        acc.Sdyy = fmaf(rd, rt.dy * rt.dy, acc.Sdyy);
+        acc.Se += re;
+        acc.Sey = fmaf(re, rt.dy, acc.Sey);
+    }
+}
+
 template <bool kGroup>
-__global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(const __grid_constant__ Batch b,
+__global__ void __launch_bounds__(kTilePix, 4) raster_bwd_kernel(const __grid_constant__ Batch b,
                                                               const float4 *__restrict__ rec,
                                                               const int *__restrict__ offsets,
                                                               const uint32_t *__restrict__ pairs, int64_t cap,
@@ -50,7 +116,8 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(const __grid_const
     // pixel state planes, two adjacent pixels per float2: B g0, B g1, B g2, A, -B g.F
     __shared__ float2 sp[5][kTilePix / 2];
     __shared__ uint32_t sorted[kGroup ? kTilePix : 1];
-    __shared__ int hist[17];
+    __shared__ uint8_t sfull[kGroup ? kTilePix : 1];
+    __shared__ int hist[kBwdKeys];
 
     const int gt = block_tile(b);
     const int v = find_view(b, gt);
@@ -79,37 +146,55 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(const __grid_const
 
     for (int cb0 = start; cb0 < end; cb0 += kTilePix) {
         uint32_t q;
+        bool full = false;
         if (kGroup) {
+            // rank this round's splats: class 0 = the whole tile lies inside the cutoff ellipse (its
+            // four corner pixels do, by a margin; the ellipse is convex, so then every pixel does
+            // and its rounded exponent stays below the cut), classes 1-16 = the 4x4-pixel cell of
+            // the centre (clamped), 17 = no record; then warps take 32 consecutive splats
             const int nr = min(kTilePix, end - cb0);
             uint32_t myq = 0xffffffffu;
-            int cell = 16, slot = 0;
-            if (tid < 16) hist[tid] = 0;
+            int key = kBwdKeys - 1, slot = 0;
+            if (tid < kBwdKeys) hist[tid] = 0;
             __syncthreads();
             if (tid < nr) {
                 myq = pairs[cb0 + tid];
-                cell = 15;
                 if (myq < nrec) {
-                    const float4 c0r = rec[3 * (int64_t)myq + 0];
+                    const float4 c0r = rec[3 * (int64_t)myq + 0], c1r = rec[3 * (int64_t)myq + 1];
+                    const SplatConsts k = splat_consts(ox, oy, c0r.x, c0r.y, c0r.z, c0r.w, c1r.y);
+                    const float lim = k.thr - fmaf(1e-3f, fabsf(k.thr), 1e-3f);
+                    bool in = true;
+#pragma unroll
+                    for (int cyy = 0; cyy < 2; ++cyy) {
+                        const RowTerms rt = row_terms(k.A2dx0, k.dy0, k.rA2, c1r.x, cyy * (kTile - 1));
+#pragma unroll
+                        for (int cxx = 0; cxx < 2; ++cxx)
+                            in = in && quad_s(col_e1(c0r.w, rt.e10, cxx * (kTile - 1)), rt.e2sq) <= lim;
+                    }
                     const int cx = f2i_clamped(floorf((c0r.x - (ox - 0.5f)) * 0.25f), 0, 3);
                     const int cy = f2i_clamped(floorf((c0r.y - (oy - 0.5f)) * 0.25f), 0, 3);
-                    cell = cy * 4 + cx;
+                    key = in ? 0 : 1 + cy * 4 + cx;
                 }
-                slot = atomicAdd(&hist[cell], 1);
+                slot = atomicAdd(&hist[key], 1);
             }
             __syncthreads();
             if (tid == 0) {
                 int run = 0;
-                for (int c = 0; c < 16; ++c) {
+                for (int c = 0; c < kBwdKeys; ++c) {
                     const int t = hist[c];
                     hist[c] = run;
                     run += t;
                 }
             }
             __syncthreads();
-            if (tid < nr) sorted[hist[cell] + slot] = myq;
+            if (tid < nr) {
+                sorted[hist[key] + slot] = myq;
+                sfull[hist[key] + slot] = key == 0 ? 1 : 0;
+            }
             __syncthreads();
             const int idx = warp * 32 + lane;
             q = idx < nr ? sorted[idx] : 0xffffffffu;
+            full = idx < nr && sfull[idx] != 0;
             if (cb0 + warp * 32 >= end) continue;  // this warp has no splat in this round
         } else {
             const int idx = cb0 + warp * 32 + lane;
@@ -136,52 +221,18 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_kernel(const __grid_const
         rhi = __reduce_max_sync(0xffffffffu, rhi);
 
         const float2 A2p = make_float2(A2, A2), wp = make_float2(w, w), l2op = make_float2(log2o, log2o);
-        const float2 m1 = make_float2(-1.f, -1.f), one2 = make_float2(1.f, 1.f);
         const float2 c0p = make_float2(a2.x, a2.x), c1p = make_float2(a2.y, a2.y), c2p = make_float2(a2.z, a2.z);
         const float2 zero2 = make_float2(0.f, 0.f);
-        float2 See = zero2, gw = zero2, gc0 = zero2, gc1 = zero2, gc2 = zero2;
-        float Se = 0.f, Sey = 0.f, Sd = 0.f, Sdy = 0.f, Sdyy = 0.f;
-        for (int ky = rlo; ky <= rhi; ++ky) {
-            const RowTerms rt = row_terms(sc.A2dx0, dy0, sc.rA2, B2, ky);
-            const float2 e10p = make_float2(rt.e10, rt.e10), e2p = make_float2(rt.e2sq, rt.e2sq);
-            float2 Rd = zero2, Re = zero2;
-#pragma unroll
-            for (int kp = 0; kp < kTile / 2; ++kp) {
-                const float2 e1 = __ffma2_rn(A2p, make_float2((float)(2 * kp), (float)(2 * kp + 1)), e10p);
-                const float2 sq = __ffma2_rn(e1, e1, e2p);
-                const bool in0 = sq.x <= sc.thr, in1 = sq.y <= sc.thr;
-                if (in0 || in1) {
-                    const int kk = ky * (kTile / 2) + kp;
-                    const float2 b0 = sp[0][kk], b1 = sp[1][kk], b2 = sp[2][kk];
-                    const float2 Ap = sp[3][kk], nbF = sp[4][kk];
-                    // log2 o - s: -s + log2 o rounds once, exactly like the forward's subtraction
-                    const float2 lg = __ffma2_rn(sq, m1, l2op);
-                    const float ar0 = fast_exp2(lg.x), ar1 = fast_exp2(lg.y);
-                    const float2 a = make_float2(in0 ? fminf(ar0, kAlphaMax) : 0.f, in1 ? fminf(ar1, kAlphaMax) : 0.f);
-                    // the alpha path (o, mu', conic) is off where alpha is clamped
-                    const float2 am = make_float2(ar0 > kAlphaMax ? 0.f : a.x, ar1 > kAlphaMax ? 0.f : a.y);
-                    const float2 D = __ffma2_rn(b0, c0p, __ffma2_rn(b1, c1p, __ffma2_rn(b2, c2p, nbF)));  // B (g.c - g.F)
-                    const float2 oma = __ffma2_rn(a, m1, one2);                                            // 1 - a
-                    const float2 inv = make_float2(fast_rcp(oma.x), fast_rcp(oma.y));
-                    const float2 dLda = __ffma2_rn(Ap, inv, __fmul2_rn(wp, D));
-                    gw = __ffma2_rn(a, D, gw);
-                    gc0 = __ffma2_rn(a, b0, gc0);  // times w in the epilogue
-                    gc1 = __ffma2_rn(a, b1, gc1);
-                    gc2 = __ffma2_rn(a, b2, gc2);
-                    const float2 da = __fmul2_rn(dLda, am);
-                    Rd = __fadd2_rn(Rd, da);
-                    const float2 qd = __fmul2_rn(da, e1);
-                    Re = __fadd2_rn(Re, qd);
-                    See = __ffma2_rn(qd, e1, See);
-                }
-            }
-            const float rd = Rd.x + Rd.y, re = Re.x + Re.y;
-            Sd += rd;
-            Sdy = fmaf(rd, rt.dy, Sdy);
-            Sdyy = fmaf(rd, rt.dy * rt.dy, Sdyy);
-            Se += re;
-            Sey = fmaf(re, rt.dy, Sey);
-        }
+        BwdAcc acc;
+        acc.See = acc.gw = acc.gc0 = acc.gc1 = acc.gc2 = zero2;
+        acc.Se = acc.Sey = acc.Sd = acc.Sdy = acc.Sdyy = 0.f;
+        const BwdSplat bs{A2p, wp, l2op, c0p, c1p, c2p, sc.A2dx0, dy0, sc.rA2, B2, sc.thr};
+        if (kGroup && __all_sync(0xffffffffu, full || !valid))
+            bwd_rows<false>(bs, sp, 0, kTile - 1, acc);  // every pixel of the tile contributes
+        else
+            bwd_rows<true>(bs, sp, rlo, rhi, acc);
+        const float Se = acc.Se, Sey = acc.Sey, Sd = acc.Sd, Sdy = acc.Sdy, Sdyy = acc.Sdyy;
+        const float2 See = acc.See, gw = acc.gw, gc0 = acc.gc0, gc1 = acc.gc1, gc2 = acc.gc2;
         if (valid) {
             const float K = -2.f * kLn2;
             const float See1 = See.x + See.y;

@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
     constexpr int kStripsPerRow = kTile / kStrip;
     __shared__ float4 s0[kFwdBatch], s1[kFwdBatch], s2[kFwdBatch];
     __shared__ float ssign[kMode == kRasterSums ? kFwdBatch : 1];
+    __shared__ uint8_t sfl[kFwdBatch];  // 1: the splat's cutoff ellipse contains the whole tile
     __shared__ float red[kFwdThreads / 32];
     __shared__ unsigned red_n[kFwdThreads / 32];
 
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
             //         s2 = (w c_r, w c_g, w c_b, w) (times the sign in sums mode)
             float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = make_float4(0.f, -INFINITY, 0.f, -1.f);
             float4 t2 = make_float4(0.f, 0.f, 0.f, 0.f);
+            bool full = false;
             if (q < nrec) {  // never written by this call's scatter otherwise: contributes nothing
                 const float4 a0 = rec[3 * (int64_t)q + 0];
                 const float4 a1 = rec[3 * (int64_t)q + 1];
@@ -75,12 +77,25 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
                 const SplatConsts c = splat_consts(ox, oy, a0.x, a0.y, a0.z, a0.w, a1.y);
                 t0 = make_float4(c.A2dx0, c.dy0, c.rA2, a0.w);
                 t1 = make_float4(a1.x, c.thr, a1.y, a1.w);
+                // the whole tile inside the cutoff ellipse: its four corner pixels are, by a margin
+                // (convexity; the margin keeps every pixel's rounded exponent below the cut)
+                const float lim = c.thr - fmaf(1e-3f, fabsf(c.thr), 1e-3f);
+                bool in = true;
+#pragma unroll
+                for (int cyy = 0; cyy < 2; ++cyy) {
+                    const RowTerms rt = row_terms(c.A2dx0, c.dy0, c.rA2, a1.x, cyy * (kTile - 1));
+#pragma unroll
+                    for (int cxx = 0; cxx < 2; ++cxx)
+                        in = in && quad_s(col_e1(a0.w, rt.e10, cxx * (kTile - 1)), rt.e2sq) <= lim;
+                }
+                full = in;
                 const float ws = kMode == kRasterSums ? a1.z * a2.w : a1.z;
                 t2 = make_float4(ws * a2.x, ws * a2.y, ws * a2.z, ws);
             }
             s0[k] = t0;
             s1[k] = t1;
             s2[k] = t2;
+            sfl[k] = full ? 1 : 0;
             if (kMode == kRasterSums) ssign[k] = q < nrec ? rec[3 * (int64_t)q + 2].w : 0.f;
         }
         __syncthreads();
@@ -92,6 +107,25 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
         const int je = min(n, jb + 32);
         for (int j = jb; j < je; ++j) {
             const float4 a0 = s0[j], a1 = s1[j];
+            if (sfl[j]) {  // block-uniform: every pixel of the tile contributes, no cutoff test
+                const RowTerms rt = row_terms(a0.x, a0.y, a0.z, a1.x, ky);
+                const float4 a2 = s2[j];
+#pragma unroll
+                for (int p = 0; p < kStrip; ++p) {
+                    const float sq = quad_s(col_e1(a0.w, rt.e10, sx + p), rt.e2sq);
+                    const float a = fminf(fast_exp2(a1.z - sq), kAlphaMax);
+                    b0[p] = fmaf(a, a2.x, b0[p]);
+                    b1[p] = fmaf(a, a2.y, b1[p]);
+                    b2[p] = fmaf(a, a2.z, b2[p]);
+                    bq[p] = fmaf(a, a2.w, bq[p]);
+                    if (kMode == kRasterSums)
+                        bl[p] = fmaf(ssign[j], log1pf(-a), bl[p]);
+                    else
+                        T[p] = fmaf(-T[p], a, T[p]);
+                    if (kCount) n_contrib += (tx * kTile + sx + p < vd.W && ty * kTile + ky < vd.H) ? 1u : 0u;
+                }
+                continue;
+            }
             // warp-uniform: the ellipse misses this warp's rows
             const float dlo = a0.y + (float)wrow;
             if (dlo > a1.w || dlo + (float)(32 / kStripsPerRow - 1) < -a1.w) continue;
