@@ -915,9 +915,43 @@ def main():
         ssim_bytes = W * H * (48 + 72 + 40)
         dssim = {"step_ms": dssim_ms, "ssim_kernels_ms": ssim_ms,
                  "ssim_gbs": ssim_bytes / (ssim_ms * 1e-3) / 1e9, "ssim_algorithmic_bytes": ssim_bytes}
+        # the stage layout: the active rows gathered once per stage, the step and Adam on them
+        with torch.cuda.stream(stream):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            spa = r.gather_active(spt, stream=stream)
+            ev1.record(stream)
+            stream.synchronize()
+            gather_ms = ev0.elapsed_time(ev1)
+            Pa = {k: getattr(spa, k) for k in PARAM_NAMES}
+            Pa["sigma"] = P["sigma"]
+            Ma = {k: torch.zeros_like(v) for k, v in Pa.items()}
+            Va = {k: torch.zeros_like(v) for k, v in Pa.items()}
+
+        def step_active_rows():
+            r.forward(spa, [cam], [0], targets=[target], stream=stream, images=[img], loss=loss)
+            r.backward(spa, stream=stream, out=out)
+
+        def train_active_rows():
+            step_active_rows()
+            r.adam_step(out, Pa, Ma, Va, lr, 100, stream=stream)
+
+        step_rows_ms = _graph_time(torch, stream, flush, step_active_rows, args.steps, args.warmup)
+        train_rows_ms = _graph_time(torch, stream, flush, train_active_rows, args.steps, args.warmup)
+        with torch.cuda.stream(stream):
+            r.set_profiling(True)
+            r.get_profile()
+            for _ in range(args.steps):
+                flush.zero_()
+                train_active_rows()
+            stream.synchronize()
+            prof_rows = r.get_profile()
+            r.set_profiling(False)
+        active_rows = {"gather_ms_per_stage": gather_ms, "step_ms": step_rows_ms, "train_iteration_ms": train_rows_ms,
+                       "per_kernel_ms": {k: v[1] / max(1, v[0]) for k, v in prof_rows.items()}}
         train = {"ms": train_ms, "adam_ms": adam_ms, "adam_gbs": adam_bytes / (adam_ms * 1e-3) / 1e9,
                  "adam_hbm_frac": adam_bytes / (adam_ms * 1e-3) / 1e9 / float(_peaks()[0].get("hbm_gbs", 6800.0)),
-                 "adam_algorithmic_bytes": adam_bytes}
+                 "adam_algorithmic_bytes": adam_bytes, "active_rows_layout": active_rows}
 
     if rank != 0:
         if ws > 1:

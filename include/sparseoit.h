@@ -87,7 +87,15 @@ typedef struct {
     int32_t width, height;
 } sparseoit_camera;
 
-/* The full splat set G (Sec. 3.1 / 3.2), device pointers, n rows each. */
+/* The splat parameters (Sec. 3.1 / 3.2), device pointers, n rows each.
+ * rows = SPARSEOIT_ROWS_BY_SPLAT: row i is splat i, n = max_splats (the
+ * full set G).  rows = SPARSEOIT_ROWS_ACTIVE: row r is the r-th active splat
+ * in the order of sparseoit_get_active, n = |A| -- the layout of an active
+ * stage (sparseoit_gather_active), read with coalesced row loads; accepted
+ * by sparseoit_forward / backward / autotune only (the frozen-sum commit
+ * and the active-set update need every splat). */
+#define SPARSEOIT_ROWS_BY_SPLAT 0
+#define SPARSEOIT_ROWS_ACTIVE 1
 typedef struct {
     const float *means;           /* [n, 3] centre mu                                 */
     const float *quats;           /* [n, 4] rotation quaternion (w, x, y, z), any norm */
@@ -98,7 +106,9 @@ typedef struct {
     int32_t sh_dtype;             /* SPARSEOIT_F32 or SPARSEOIT_BF16                  */
     float sigma;                  /* scene depth scale of Eq. 1 (> 0)                 */
     float bg[3];                  /* background colour c0 of Eq. 7                    */
-    int64_t n;                    /* number of splats (== max_splats of the context)  */
+    int64_t n;                    /* number of rows (max_splats, or |A| for ROWS_ACTIVE) */
+    int32_t rows;                 /* SPARSEOIT_ROWS_BY_SPLAT or SPARSEOIT_ROWS_ACTIVE */
+    int32_t reserved;
 } sparseoit_splats;
 
 /* Gradient outputs, device pointers.  Only active splats receive gradients
@@ -344,6 +354,8 @@ typedef struct {
                          sh_weight, sigma */
     float beta1, beta2, eps;
     int32_t step;     /* t >= 1: the bias corrections are 1 - beta^t */
+    int32_t rows;     /* layout of params, m and v: SPARSEOIT_ROWS_BY_SPLAT (N rows) or
+                         SPARSEOIT_ROWS_ACTIVE (|A| rows in active order, like the gradients) */
 } sparseoit_adam;
 
 /* Sparse Adam over the active set: for every active splat (the context's
@@ -352,14 +364,24 @@ typedef struct {
  *   p -= (lr / (1 - b1^t)) m / (sqrt(v) / sqrt(1 - b2^t) + eps)
  * (the torch.optim.Adam step).  grads: the compact rows of the last
  * sparseoit_backward (rows_by_splat = 0, N_A rows in active order; grads->sigma
- * = dL/dsigma); params, m, v: full rows indexed by splat, updated in place;
- * rows of inactive splats are neither read nor written.  sigma (params,
+ * = dL/dsigma); params, m, v: rows by splat or active rows (cfg->rows),
+ * updated in place; rows of inactive splats are neither read nor written.  sigma (params,
  * m, v ->sigma, all non-null or all null) is updated with lr[7].  The
  * caller copies the new sigma into sparseoit_splats.sigma (a host value)
  * before the next forward, and recommits the frozen sums if it changed.
  * Asynchronous on `stream`. */
 int sparseoit_adam_step(sparseoit_ctx *ctx, const sparseoit_grads *grads, sparseoit_rows *params, sparseoit_rows *m,
                         sparseoit_rows *v, const sparseoit_adam *cfg, void *stream);
+
+/* Stage layout (Sec. 4.1: between two active-set updates only A is
+ * optimised): copy the active rows of a full row set (rows by splat) into
+ * active rows (|A| rows in active order), or back.  FP32 arrays except
+ * sh_color / sh_weight, whose element type is sh_dtype; the sigma fields
+ * are not read.  Asynchronous on `stream`. */
+int sparseoit_gather_active(sparseoit_ctx *ctx, const sparseoit_rows *full, sparseoit_rows *active, int32_t sh_dtype,
+                            void *stream);
+int sparseoit_scatter_active(sparseoit_ctx *ctx, const sparseoit_rows *active, sparseoit_rows *full, int32_t sh_dtype,
+                             void *stream);
 
 /* Allocation-free active-index compaction.  The paper has no counterpart:
  * this entry point serves callers that cannot allocate device memory --

@@ -23,6 +23,8 @@ F32 = 0
 BF16 = 1
 COMMIT_INCREMENTAL = 0
 COMMIT_RECOMPUTE = 1
+ROWS_BY_SPLAT = 0
+ROWS_ACTIVE = 1
 MAX_BATCH_VIEWS = 32
 
 ERROR_NAMES = {ERR_INVALID_ARG: "INVALID_ARG", ERR_OOM: "OOM", ERR_CUDA: "CUDA", ERR_STATE: "STATE",
@@ -35,7 +37,8 @@ EXPORTED = (
     "sparseoit_reserve_pairs", "sparseoit_status", "sparseoit_last_counts", "sparseoit_set_counting",
     "sparseoit_set_profiling", "sparseoit_get_profile", "sparseoit_last_error", "sparseoit_version",
     "sparseoit_compact_active_static", "sparseoit_autotune", "sparseoit_fps_views", "sparseoit_activeness",
-    "sparseoit_update_active_set", "sparseoit_adam_step", "sparseoit_loss_l1_dssim",
+    "sparseoit_update_active_set", "sparseoit_adam_step", "sparseoit_loss_l1_dssim", "sparseoit_gather_active",
+    "sparseoit_scatter_active",
 )
 STATIC_MAX_SPLATS = 16 * 1024 * 1024
 
@@ -48,7 +51,7 @@ class Rows(ctypes.Structure):
 
 class Adam(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_float * 8), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
-                ("eps", ctypes.c_float), ("step", ctypes.c_int32)]
+                ("eps", ctypes.c_float), ("step", ctypes.c_int32), ("rows", ctypes.c_int32)]
 
 
 class Camera(ctypes.Structure):
@@ -61,7 +64,7 @@ class Splats(ctypes.Structure):
     _fields_ = [("means", ctypes.c_void_p), ("quats", ctypes.c_void_p), ("log_scales", ctypes.c_void_p),
                 ("opacity_logits", ctypes.c_void_p), ("sh_color", ctypes.c_void_p), ("sh_weight", ctypes.c_void_p),
                 ("sh_dtype", ctypes.c_int32), ("sigma", ctypes.c_float), ("bg", ctypes.c_float * 3),
-                ("n", ctypes.c_int64)]
+                ("n", ctypes.c_int64), ("rows", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Grads(ctypes.Structure):
@@ -126,6 +129,8 @@ def load(path: str = LIB_PATH):
             "sparseoit_update_active_set": ([vp, P(Splats), P(Camera), i32, P(vp), i32, i32, P(ctypes.c_float),
                                              P(Grads), vp, P(i32), vp], ctypes.c_int),
             "sparseoit_loss_l1_dssim": ([vp, P(vp), ctypes.c_float, vp, P(vp), P(ctypes.c_float), vp], ctypes.c_int),
+            "sparseoit_gather_active": ([vp, P(Rows), P(Rows), i32, vp], ctypes.c_int),
+            "sparseoit_scatter_active": ([vp, P(Rows), P(Rows), i32, vp], ctypes.c_int),
             "sparseoit_adam_step": ([vp, P(Grads), P(Rows), P(Rows), P(Rows), P(Adam), vp], ctypes.c_int),
             "sparseoit_activeness": ([P(Grads), i64, P(ctypes.c_float), vp, vp, vp], ctypes.c_int),
         }

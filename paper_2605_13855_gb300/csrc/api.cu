@@ -57,7 +57,7 @@ struct sparseoit_ctx {
     int64_t *d_npairs = nullptr;
     unsigned long long *d_contrib = nullptr;
     bool counting = false;
-    float *d_ssim_abc = nullptr;   // D-SSIM: 9 planes of the largest view
+    float *d_ssim_abc = nullptr;   // D-SSIM: 9 partials per pixel of the largest view
     double *d_ssim_sums = nullptr; // D-SSIM: 2 sums per view of a batch
     float *d_upd_image = nullptr;  // image and loss of the active-set update's full-set renders
     float *d_upd_loss = nullptr;
@@ -141,9 +141,18 @@ static cudaError_t grow(T **p, int64_t *cap, int64_t want) {
     return e;
 }
 
-static int check_splats(sparseoit_ctx *ctx, const sparseoit_splats *s) {
+static int check_splats(sparseoit_ctx *ctx, const sparseoit_splats *s, bool allow_active_rows) {
     if (!s) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "splats is null");
-    if (s->n != ctx->N) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "splats->n differs from max_splats");
+    if (s->rows == SPARSEOIT_ROWS_ACTIVE) {
+        if (!allow_active_rows)
+            return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "this call needs the splats in rows by splat");
+        if (!ctx->have_mask) return fail(ctx, SPARSEOIT_ERR_STATE, "active rows before set_active");
+        if (s->n != ctx->n_active) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "splats->n differs from |A|");
+    } else if (s->rows != SPARSEOIT_ROWS_BY_SPLAT) {
+        return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "unknown splats->rows");
+    } else if (s->n != ctx->N) {
+        return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "splats->n differs from max_splats");
+    }
     if (!s->means || !s->quats || !s->log_scales || !s->opacity_logits || !s->sh_color || !s->sh_weight)
         return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "a splat parameter pointer is null");
     if (((uintptr_t)s->quats & 15u) != 0)
@@ -164,6 +173,7 @@ static SplatPtrs splat_ptrs(const sparseoit_splats *s) {
     p.sh_weight = s->sh_weight;
     p.sigma = s->sigma;
     for (int k = 0; k < 3; ++k) p.bg[k] = s->bg[k];
+    p.active_rows = s->rows == SPARSEOIT_ROWS_ACTIVE ? 1 : 0;
     return p;
 }
 
@@ -402,7 +412,7 @@ int sparseoit_get_frozen(sparseoit_ctx *ctx, int32_t view, float **d_planes) {
 int sparseoit_commit_frozen(sparseoit_ctx *ctx, const sparseoit_splats *splats, const sparseoit_camera *cam,
                             int32_t view, int32_t mode, void *stream) {
     if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
-    int rc = check_splats(ctx, splats);
+    int rc = check_splats(ctx, splats, false);
     if (rc) return rc;
     if (!ctx->have_mask) return fail(ctx, SPARSEOIT_ERR_STATE, "commit before set_active");
     if (mode != SPARSEOIT_COMMIT_INCREMENTAL && mode != SPARSEOIT_COMMIT_RECOMPUTE)
@@ -447,7 +457,7 @@ int sparseoit_forward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const 
                       const int32_t *views, int32_t n_views, float *const *d_images, const float *const *d_targets,
                       float *d_loss, void *stream) {
     if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
-    int rc = check_splats(ctx, splats);
+    int rc = check_splats(ctx, splats, true);
     if (rc) return rc;
     if (!ctx->have_mask) return fail(ctx, SPARSEOIT_ERR_STATE, "forward before set_active");
     if (n_views < 1 || n_views > kMaxViews || !cams || !views || !d_images)
@@ -508,7 +518,7 @@ int sparseoit_forward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const 
 int sparseoit_backward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const float *const *d_grad_images,
                        sparseoit_grads *out, void *stream) {
     if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
-    int rc = check_splats(ctx, splats);
+    int rc = check_splats(ctx, splats, true);
     if (rc) return rc;
     if (!ctx->have_fwd || ctx->last_generation != ctx->generation)
         return fail(ctx, SPARSEOIT_ERR_STATE, "backward without a matching forward");
@@ -640,6 +650,9 @@ int sparseoit_adam_step(sparseoit_ctx *ctx, const sparseoit_grads *grads, sparse
     a.eps = cfg->eps;
     a.idx = ctx->d_idx_active;
     a.n_active = ctx->n_active;
+    if (cfg->rows != SPARSEOIT_ROWS_BY_SPLAT && cfg->rows != SPARSEOIT_ROWS_ACTIVE)
+        return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "adam: unknown rows layout");
+    a.active_rows = cfg->rows == SPARSEOIT_ROWS_ACTIVE ? 1 : 0;
     if (sig) {
         a.sigma_g = grads->sigma;
         a.sigma_p = params->sigma;
@@ -697,6 +710,37 @@ int sparseoit_loss_l1_dssim(sparseoit_ctx *ctx, const float *const *d_targets, f
     CK_LAUNCH("ssim_loss_kernel");
     ctx->last_fused = true;  // the state planes now hold the backward state
     return SPARSEOIT_OK;
+}
+
+static int rows_copy(sparseoit_ctx *ctx, const sparseoit_rows *src, sparseoit_rows *dst, int32_t sh_dtype,
+                     bool to_active, void *stream) {
+    if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
+    if (!src || !dst) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "rows: null argument");
+    if (!ctx->have_mask) return fail(ctx, SPARSEOIT_ERR_STATE, "rows: before set_active");
+    if (sh_dtype != SPARSEOIT_F32 && sh_dtype != SPARSEOIT_BF16)
+        return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "rows: unknown sh_dtype");
+    const float *s6[6] = {src->means, src->quats, src->log_scales, src->opacity_logits, src->sh_color, src->sh_weight};
+    float *d6[6] = {dst->means, dst->quats, dst->log_scales, dst->opacity_logits, dst->sh_color, dst->sh_weight};
+    const int width[6] = {3, 4, 3, 1, 48, 16};
+    for (int k = 0; k < 6; ++k)
+        if (!s6[k] || !d6[k]) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "rows: null array");
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int k = 0; k < 6; ++k) {
+        const int eb = (k >= 4 && sh_dtype == SPARSEOIT_BF16) ? 2 : 4;
+        soit::launch_rows_copy(ctx->d_idx_active, ctx->n_active, width[k], s6[k], d6[k], eb, to_active, st);
+        CK_LAUNCH("rows_copy_kernel");
+    }
+    return SPARSEOIT_OK;
+}
+
+int sparseoit_gather_active(sparseoit_ctx *ctx, const sparseoit_rows *full, sparseoit_rows *active, int32_t sh_dtype,
+                            void *stream) {
+    return rows_copy(ctx, full, active, sh_dtype, true, stream);
+}
+
+int sparseoit_scatter_active(sparseoit_ctx *ctx, const sparseoit_rows *active, sparseoit_rows *full, int32_t sh_dtype,
+                             void *stream) {
+    return rows_copy(ctx, active, full, sh_dtype, false, stream);
 }
 
 int sparseoit_autotune(sparseoit_ctx *ctx, const sparseoit_splats *splats, const sparseoit_camera *cams,

@@ -72,6 +72,7 @@ struct SplatPtrs {
     const void *sh_color, *sh_weight;
     float sigma;
     float bg[3];
+    int active_rows;  // 1: row r of every array is the r-th active splat (else row i is splat i)
 };
 
 __device__ __forceinline__ int find_view(const Batch &b, int gt) {

@@ -55,8 +55,12 @@ struct AdamArgs {
     float beta1, beta2, eps;
     const float *sigma_g;
     float *sigma_p, *sigma_m, *sigma_v;  // null: sigma not updated
+    int active_rows;              // 1: p, m, v hold |A| rows in active order (like g)
 };
 int launch_adam(const AdamArgs &a, cudaStream_t st);
+// Copy the active rows of one [N, w] array into [n_active, w] (to_active) or back; elem_bytes 4 or 2.
+int launch_rows_copy(const int *idx, int64_t n_active, int w, const void *src, void *dst, int elem_bytes,
+                     bool to_active, cudaStream_t st);
 
 // D-SSIM loss (ssim.cu): the 11-tap Gaussian window, per-view loss constants.
 struct SsimWindow {
@@ -67,7 +71,7 @@ struct SsimLossArgs {
     double lambda;
     double inv_n[kMaxViews];  // 1 / (3 H W) per view
 };
-// One view: abc = 9 planes of H W floats (scratch), sums = 2 doubles (S, |x - y|), state = the view's
+// One view: abc = [H, W, 9] floats (scratch), sums = 2 doubles (S, |x - y|), state = the view's
 // five planes (F, T, Q in; the backward state out), grad_out = dL/dC [H, W, 3] or null.
 int launch_ssim_view(const float *img, const float *tgt, int W, int H, const SsimWindow &win, float *abc,
                      double *sums, float lambda, const float bg[3], float *state, float *grad_out, cudaStream_t st);

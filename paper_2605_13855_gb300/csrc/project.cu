@@ -82,7 +82,8 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Ba
     const int k = threadIdx.x & (G - 1);
     const int n_list = n1 + n2;
     if (r >= n_list) return;  // whole groups leave together
-    const int i = r < n1 ? list1[r] : list2[r - n1];
+    // parameter row: the splat's own row, or (active rows, forward only) the list entry itself
+    const int i = sp.active_rows ? r : (r < n1 ? list1[r] : list2[r - n1]);
     const float sign = r < n1 ? 1.f : -1.f;
 
     float mu[3], q[4], ls[3];

@@ -18,15 +18,16 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(const __grid_constant_
     float gsig_local = 0.f;
     if (r < n) {
         const int i = list[r];
+        const int pi = sp.active_rows ? r : i;  // parameter row
         float mu[3], q[4], ls[3];
-        for (int k = 0; k < 3; ++k) mu[k] = __ldg(sp.means + 3 * (int64_t)i + k);
-        const float4 q4 = __ldg(reinterpret_cast<const float4 *>(sp.quats) + i);
+        for (int k = 0; k < 3; ++k) mu[k] = __ldg(sp.means + 3 * (int64_t)pi + k);
+        const float4 q4 = __ldg(reinterpret_cast<const float4 *>(sp.quats) + pi);
         q[0] = q4.x; q[1] = q4.y; q[2] = q4.z; q[3] = q4.w;
-        for (int k = 0; k < 3; ++k) ls[k] = __ldg(sp.log_scales + 3 * (int64_t)i + k);
-        const float ol = __ldg(sp.opacity_logits + i);
+        for (int k = 0; k < 3; ++k) ls[k] = __ldg(sp.log_scales + 3 * (int64_t)pi + k);
+        const float ol = __ldg(sp.opacity_logits + pi);
         const float o = 1.f / (1.f + expf(-ol));
-        const ShT *hc = reinterpret_cast<const ShT *>(sp.sh_color) + 48 * (int64_t)i;
-        const ShT *hw = reinterpret_cast<const ShT *>(sp.sh_weight) + 16 * (int64_t)i;
+        const ShT *hc = reinterpret_cast<const ShT *>(sp.sh_color) + 48 * (int64_t)pi;
+        const ShT *hw = reinterpret_cast<const ShT *>(sp.sh_weight) + 16 * (int64_t)pi;
 
         float g_mu[3] = {0.f, 0.f, 0.f}, g_q[4] = {0.f, 0.f, 0.f, 0.f}, g_ls[3] = {0.f, 0.f, 0.f}, g_ol = 0.f;
         float g_h[48], g_hw[16];

@@ -12,8 +12,9 @@
 //
 // Two passes per view, both on 32 x 16 output tiles with a 5-pixel halo held
 // in shared memory and the separable window applied rows first:
-//   ssim_fwd_kernel (one channel per block): the five filtered moments, S and
-//     (a, b, c) per pixel; block sums of S and |x - y| into per-view doubles;
+//   ssim_fwd_kernel (all channels per block): the five filtered moments, S and
+//     (a, b, c) per pixel and channel, written interleaved [H, W, 9]; block
+//     sums of S and |x - y| into per-view doubles;
 //   ssim_bwd_kernel (all channels per block): filters (a, b, c), forms
 //     dL/dC and rewrites the forward's (F, T, Q) planes into the pixel state
 //     (B g, A, -B g.F) that the backward raster reads.
@@ -26,72 +27,78 @@ constexpr int kSsimTW = 32, kSsimTH = 16, kSsimR = 5, kSsimK = 2 * kSsimR + 1;
 constexpr int kSsimHW = kSsimTW + 2 * kSsimR, kSsimHH = kSsimTH + 2 * kSsimR;  // 42 x 26 halo tile
 constexpr float kSsimC1 = 0.01f * 0.01f, kSsimC2 = 0.03f * 0.03f;
 
-// Loads the halo tile of one plane (value(x, y) given by the functor) with zeros outside the image.
-template <typename F>
-__device__ __forceinline__ void load_halo(float (*dst)[kSsimHW], int x0, int y0, int W, int H, F value) {
-    for (int i = threadIdx.x; i < kSsimHH * kSsimHW; i += blockDim.x) {
-        const int r = i / kSsimHW, c = i - r * kSsimHW;
-        const int gy = y0 - kSsimR + r, gx = x0 - kSsimR + c;
-        dst[r][c] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? value(gx, gy) : 0.f;
+// Loads the halo tile of C interleaved values per pixel (rows of (42 C)
+// contiguous floats of a [H, W, C] image, coalesced) into dst[r][c * C + j],
+// zeros outside the image.
+template <int C>
+__device__ __forceinline__ void load_halo(float *__restrict__ dst, const float *__restrict__ src, int x0, int y0, int W,
+                                          int H) {
+    constexpr int RW = kSsimHW * C;
+    for (int i = threadIdx.x; i < kSsimHH * RW; i += blockDim.x) {
+        const int r = i / RW, e = i - r * RW;
+        const int gy = y0 - kSsimR + r, gx = x0 - kSsimR + e / C;
+        dst[i] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? src[((int64_t)gy * W + gx) * C + (e % C)] : 0.f;
     }
 }
 
+// One block per 32 x 16 tile, all three channels: the image and target halo
+// tiles are read once (interleaved, coalesced); per channel the five moments
+// are filtered (rows, then columns) and S, a, b, c formed.  abc: [H, W, 9]
+// (a, b, c of channel 0, then 1, then 2).
 __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *__restrict__ img, const float *__restrict__ tgt,
                                                        int W, int H, SsimWindow win, float *__restrict__ abc,
                                                        double *__restrict__ sums) {
-    __shared__ float xs[kSsimHH][kSsimHW], ys[kSsimHH][kSsimHW];
+    __shared__ float xs[kSsimHH * kSsimHW * 3], ys[kSsimHH * kSsimHW * 3];
     __shared__ float hs[5][kSsimHH][kSsimTW];
     __shared__ float red[2][8];
-    const int ch = blockIdx.z;
     const int x0 = blockIdx.x * kSsimTW, y0 = blockIdx.y * kSsimTH;
-    const int tid = threadIdx.x;
-    load_halo(xs, x0, y0, W, H, [&](int gx, int gy) { return img[3 * ((int64_t)gy * W + gx) + ch]; });
-    load_halo(ys, x0, y0, W, H, [&](int gx, int gy) { return tgt[3 * ((int64_t)gy * W + gx) + ch]; });
-    __syncthreads();
-    for (int i = tid; i < kSsimHH * kSsimTW; i += blockDim.x) {
-        const int r = i / kSsimTW, c = i - r * kSsimTW;
-        float sx = 0.f, sy = 0.f, sxx = 0.f, syy = 0.f, sxy = 0.f;
-#pragma unroll
-        for (int k = 0; k < kSsimK; ++k) {
-            const float w = win.w[k], xv = xs[r][c + k], yv = ys[r][c + k];
-            sx = fmaf(w, xv, sx);
-            sy = fmaf(w, yv, sy);
-            sxx = fmaf(w, xv * xv, sxx);
-            syy = fmaf(w, yv * yv, syy);
-            sxy = fmaf(w, xv * yv, sxy);
-        }
-        hs[0][r][c] = sx;
-        hs[1][r][c] = sy;
-        hs[2][r][c] = sxx;
-        hs[3][r][c] = syy;
-        hs[4][r][c] = sxy;
-    }
-    __syncthreads();
-    const int tx = tid & 31, ty = tid >> 5;
-    const int64_t HW = (int64_t)W * H;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    load_halo<3>(xs, img, x0, y0, W, H);
+    load_halo<3>(ys, tgt, x0, y0, W, H);
     float s_sum = 0.f, l1_sum = 0.f;
-    for (int rr = ty; rr < kSsimTH; rr += 8) {
-        const int gx = x0 + tx, gy = y0 + rr;
-        if (gx >= W || gy >= H) continue;
-        float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int ch = 0; ch < 3; ++ch) {
+        __syncthreads();
+        for (int i = tid; i < kSsimHH * kSsimTW; i += blockDim.x) {
+            const int r = i / kSsimTW, c = i - r * kSsimTW;
+            const float *xr = xs + (r * kSsimHW + c) * 3 + ch, *yr = ys + (r * kSsimHW + c) * 3 + ch;
+            float sx = 0.f, sy = 0.f, sxx = 0.f, syy = 0.f, sxy = 0.f;
 #pragma unroll
-        for (int k = 0; k < kSsimK; ++k)
+            for (int k = 0; k < kSsimK; ++k) {
+                const float w = win.w[k], xv = xr[3 * k], yv = yr[3 * k];
+                sx = fmaf(w, xv, sx);
+                sy = fmaf(w, yv, sy);
+                sxx = fmaf(w, xv * xv, sxx);
+                syy = fmaf(w, yv * yv, syy);
+                sxy = fmaf(w, xv * yv, sxy);
+            }
+            hs[0][r][c] = sx;
+            hs[1][r][c] = sy;
+            hs[2][r][c] = sxx;
+            hs[3][r][c] = syy;
+            hs[4][r][c] = sxy;
+        }
+        __syncthreads();
+        for (int rr = ty; rr < kSsimTH; rr += 8) {
+            const int gx = x0 + tx, gy = y0 + rr;
+            if (gx >= W || gy >= H) continue;
+            float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int q = 0; q < 5; ++q) m[q] = fmaf(win.w[k], hs[q][rr + k][tx], m[q]);
-        const float mx = m[0], my = m[1];
-        const float sxx = m[2] - mx * mx, syy = m[3] - my * my, sxy = m[4] - mx * my;
-        const float A = 2.f * mx * my + kSsimC1, B = 2.f * sxy + kSsimC2;
-        const float Cc = mx * mx + my * my + kSsimC1, D = sxx + syy + kSsimC2;
-        const float S = (A * B) / (Cc * D);
-        const float a = S * (2.f * my / A - 2.f * my / B - 2.f * mx / Cc + 2.f * mx / D);
-        const float b = -S / D;
-        const float c = 2.f * S / B;
-        const int64_t pix = (int64_t)gy * W + gx;
-        abc[(3 * ch + 0) * HW + pix] = a;
-        abc[(3 * ch + 1) * HW + pix] = b;
-        abc[(3 * ch + 2) * HW + pix] = c;
-        s_sum += S;
-        l1_sum += fabsf(xs[rr + kSsimR][tx + kSsimR] - ys[rr + kSsimR][tx + kSsimR]);
+            for (int k = 0; k < kSsimK; ++k)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) m[q] = fmaf(win.w[k], hs[q][rr + k][tx], m[q]);
+            const float mx = m[0], my = m[1];
+            const float sxx = m[2] - mx * mx, syy = m[3] - my * my, sxy = m[4] - mx * my;
+            const float A = 2.f * mx * my + kSsimC1, B = 2.f * sxy + kSsimC2;
+            const float Cc = mx * mx + my * my + kSsimC1, D = sxx + syy + kSsimC2;
+            const float S = (A * B) / (Cc * D);
+            float *o = abc + ((int64_t)gy * W + gx) * 9 + 3 * ch;
+            o[0] = S * (2.f * my / A - 2.f * my / B - 2.f * mx / Cc + 2.f * mx / D);  // dS/dmu_x
+            o[1] = -S / D;                                                              // dS/dE[xx]
+            o[2] = 2.f * S / B;                                                         // dS/dE[xy]
+            s_sum += S;
+            const int ci = ((rr + kSsimR) * kSsimHW + tx + kSsimR) * 3 + ch;
+            l1_sum += fabsf(xs[ci] - ys[ci]);
+        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -104,36 +111,50 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *__restrict__
     }
     __syncthreads();
     if (tid == 0) {
-        double s = 0.0, l = 0.0;
+        double sv = 0.0, lv = 0.0;
         for (int k = 0; k < 8; ++k) {
-            s += red[0][k];
-            l += red[1][k];
+            sv += red[0][k];
+            lv += red[1][k];
         }
-        atomicAdd(sums + 0, s);
-        atomicAdd(sums + 1, l);
+        atomicAdd(sums + 0, sv);
+        atomicAdd(sums + 1, lv);
     }
 }
 
+// One block per 32 x 16 tile: per channel, the (a, b, c) halo tile is read
+// once (interleaved) and filtered; dL/dC per pixel, then the state rewrite.
 __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *__restrict__ img, const float *__restrict__ tgt,
                                                        int W, int H, SsimWindow win, const float *__restrict__ abc,
                                                        float lambda, float bg0, float bg1, float bg2,
                                                        float *__restrict__ state, float *__restrict__ grad_out) {
-    __shared__ float ms[kSsimHH][kSsimHW];
+    __shared__ float ms[kSsimHH * kSsimHW * 3];
     __shared__ float hs[9][kSsimHH][kSsimTW];
     const int x0 = blockIdx.x * kSsimTW, y0 = blockIdx.y * kSsimTH;
     const int tid = threadIdx.x;
     const int64_t HW = (int64_t)W * H;
-    for (int q = 0; q < 9; ++q) {
-        const float *plane = abc + q * HW;
+    for (int ch = 0; ch < 3; ++ch) {
         __syncthreads();
-        load_halo(ms, x0, y0, W, H, [&](int gx, int gy) { return plane[(int64_t)gy * W + gx]; });
+        // the three partials of this channel: a halo of a [H, W, 9] array restricted to 3 values
+        for (int i = tid; i < kSsimHH * kSsimHW * 3; i += blockDim.x) {
+            const int r = i / (kSsimHW * 3), e = i - r * (kSsimHW * 3);
+            const int gy = y0 - kSsimR + r, gx = x0 - kSsimR + e / 3;
+            ms[i] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? abc[((int64_t)gy * W + gx) * 9 + 3 * ch + e % 3]
+                                                              : 0.f;
+        }
         __syncthreads();
         for (int i = tid; i < kSsimHH * kSsimTW; i += blockDim.x) {
             const int r = i / kSsimTW, c = i - r * kSsimTW;
-            float s = 0.f;
+            const float *mr = ms + (r * kSsimHW + c) * 3;
+            float fa = 0.f, fb = 0.f, fc = 0.f;
 #pragma unroll
-            for (int k = 0; k < kSsimK; ++k) s = fmaf(win.w[k], ms[r][c + k], s);
-            hs[q][r][c] = s;
+            for (int k = 0; k < kSsimK; ++k) {
+                fa = fmaf(win.w[k], mr[3 * k + 0], fa);
+                fb = fmaf(win.w[k], mr[3 * k + 1], fb);
+                fc = fmaf(win.w[k], mr[3 * k + 2], fc);
+            }
+            hs[3 * ch + 0][r][c] = fa;
+            hs[3 * ch + 1][r][c] = fb;
+            hs[3 * ch + 2][r][c] = fc;
         }
     }
     __syncthreads();
@@ -185,10 +206,9 @@ __global__ void ssim_loss_kernel(const double *__restrict__ sums, const __grid_c
 
 int launch_ssim_view(const float *img, const float *tgt, int W, int H, const SsimWindow &win, float *abc,
                      double *sums, float lambda, const float bg[3], float *state, float *grad_out, cudaStream_t st) {
-    const dim3 grid((W + kSsimTW - 1) / kSsimTW, (H + kSsimTH - 1) / kSsimTH, 3);
+    const dim3 grid((W + kSsimTW - 1) / kSsimTW, (H + kSsimTH - 1) / kSsimTH, 1);
     ssim_fwd_kernel<<<grid, 256, 0, st>>>(img, tgt, W, H, win, abc, sums);
-    const dim3 grid2(grid.x, grid.y, 1);
-    ssim_bwd_kernel<<<grid2, 256, 0, st>>>(img, tgt, W, H, win, abc, lambda, bg[0], bg[1], bg[2], state, grad_out);
+    ssim_bwd_kernel<<<grid, 256, 0, st>>>(img, tgt, W, H, win, abc, lambda, bg[0], bg[1], bg[2], state, grad_out);
     return 0;
 }
 

@@ -34,6 +34,7 @@ class SplatParams:
     sh_weight: torch.Tensor       # [N, 16]    float32 or bfloat16
     sigma: float = 6.0
     bg: Sequence[float] = field(default_factory=lambda: (0.0, 0.0, 0.0))
+    active_rows: bool = False     # rows are the active splats in active order (Renderer.gather_active)
 
     @property
     def n(self) -> int:
@@ -79,6 +80,7 @@ def splats_struct(p: SplatParams) -> _lib.Splats:
     for k in range(3):
         s.bg[k] = float(p.bg[k])
     s.n = n
+    s.rows = _lib.ROWS_ACTIVE if p.active_rows else _lib.ROWS_BY_SPLAT
     return s
 
 
@@ -345,18 +347,15 @@ class Renderer:
                   beta2: float = 0.999, eps: float = 1e-15, stream=None):
         """Sparse Adam over the active rows (sparseoit_adam_step), in place on params / m / v.
 
-        grads: compact rows of the last backward (active order); params, m, v: full rows by splat
-        (dicts of FP32 CUDA tensors with the parameter names, plus optional "sigma" [1] in all four).
+        grads: compact rows of the last backward (active order); params, m, v: full rows by splat,
+        or active rows (|A| rows, the layout of gather_active) -- dicts of FP32 CUDA tensors with the
+        parameter names, plus optional "sigma" [1] in all four.
         lr: 8 rates (means, quats, log_scales, opacity, SH colour degree 0, degrees 1-3, SH weight, sigma)."""
+        nrow = params["means"].shape[0]
+        active_rows = nrow == self.n_active and nrow != self.n
+
         def rows(d):
-            r = _lib.Rows()
-            for name in PARAM_NAMES:
-                t = d[name]
-                if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.shape[0] != self.n:
-                    raise ValueError(f"{name} must be contiguous float32 CUDA with {self.n} rows")
-                setattr(r, name, t.data_ptr())
-            r.sigma = d["sigma"].data_ptr() if "sigma" in d else 0
-            return r
+            return self._rows_struct(d, nrow)
         g = _lib.Grads()
         for name in PARAM_NAMES:
             setattr(g, name, grads[name].data_ptr())
@@ -368,9 +367,45 @@ class Renderer:
         for k in range(8):
             cfg.lr[k] = float(lr[k])
         cfg.beta1, cfg.beta2, cfg.eps, cfg.step = float(beta1), float(beta2), float(eps), int(step)
+        cfg.rows = _lib.ROWS_ACTIVE if active_rows else _lib.ROWS_BY_SPLAT
         self._check(self.lib.sparseoit_adam_step(self._ctx, ctypes.byref(g), ctypes.byref(rp), ctypes.byref(rm),
                                                  ctypes.byref(rv), ctypes.byref(cfg),
                                                  ctypes.c_void_p(_stream_ptr(stream))))
+
+    @staticmethod
+    def _rows_struct(d: Dict[str, torch.Tensor], n: int, sh_dtype=None) -> "_lib.Rows":
+        r = _lib.Rows()
+        for name in PARAM_NAMES:
+            t = d[name]
+            want = torch.float32 if name not in ("sh_color", "sh_weight") or sh_dtype is None else sh_dtype
+            if t.dtype != want or not t.is_cuda or not t.is_contiguous() or t.shape[0] != n:
+                raise ValueError(f"{name} must be contiguous {want} CUDA with {n} rows")
+            setattr(r, name, t.data_ptr())
+        r.sigma = d["sigma"].data_ptr() if "sigma" in d else 0
+        return r
+
+    def gather_active(self, full: SplatParams, stream=None) -> SplatParams:
+        """The active rows of `full` (rows by splat) as a new SplatParams in active order
+        (sparseoit_gather_active): the stage layout read by forward / backward / adam_step."""
+        na = self.n_active
+        shdt = full.sh_color.dtype
+        act = {name: torch.empty((na,) + PARAM_SHAPES[name], dtype=getattr(full, name).dtype, device="cuda")
+               for name in PARAM_NAMES}
+        src = self._rows_struct({k: getattr(full, k) for k in PARAM_NAMES}, self.n, shdt)
+        dst = self._rows_struct(act, na, shdt)
+        self._check(self.lib.sparseoit_gather_active(self._ctx, ctypes.byref(src), ctypes.byref(dst),
+                                                     _lib.BF16 if shdt == torch.bfloat16 else _lib.F32,
+                                                     ctypes.c_void_p(_stream_ptr(stream))))
+        return SplatParams(*[act[k] for k in PARAM_NAMES], full.sigma, full.bg, active_rows=True)
+
+    def scatter_active(self, active: SplatParams, full: SplatParams, stream=None):
+        """Write the active rows back into `full` (sparseoit_scatter_active)."""
+        shdt = full.sh_color.dtype
+        src = self._rows_struct({k: getattr(active, k) for k in PARAM_NAMES}, self.n_active, shdt)
+        dst = self._rows_struct({k: getattr(full, k) for k in PARAM_NAMES}, self.n, shdt)
+        self._check(self.lib.sparseoit_scatter_active(self._ctx, ctypes.byref(src), ctypes.byref(dst),
+                                                      _lib.BF16 if shdt == torch.bfloat16 else _lib.F32,
+                                                      ctypes.c_void_p(_stream_ptr(stream))))
 
     # ------------------------------------------------------------ misc
     def status(self, stream=None):

@@ -202,7 +202,11 @@ def test_permutation_invariance_gpu():
     r2, sp2 = _renderer_for(sc2, [cam], mask)
     a = to_np(r1.forward(sp1, [cam], [0])[0][0])
     b = to_np(r2.forward(sp2, [cam], [0])[0][0])
-    assert np.abs(a - b).max() <= 1e-6 * np.abs(a).max()
+    # the pairs of a tile are summed in scatter order (any order is correct, App. A): the two
+    # renders differ by FP32 re-association only, a few ulps of the per-pixel sums
+    d = np.abs(a - b)
+    assert d.max() <= 4e-6 * np.abs(a).max()
+    assert d.mean() <= 1e-7 * np.abs(a).max()
 
 
 def test_state_and_capacity_errors():
