@@ -27,77 +27,95 @@ constexpr int kSsimTW = 32, kSsimTH = 16, kSsimR = 5, kSsimK = 2 * kSsimR + 1;
 constexpr int kSsimHW = kSsimTW + 2 * kSsimR, kSsimHH = kSsimTH + 2 * kSsimR;  // 42 x 26 halo tile
 constexpr float kSsimC1 = 0.01f * 0.01f, kSsimC2 = 0.03f * 0.03f;
 
-// Loads the halo tile of C interleaved values per pixel (rows of (42 C)
-// contiguous floats of a [H, W, C] image, coalesced) into dst[r][c * C + j],
-// zeros outside the image.
-template <int C>
-__device__ __forceinline__ void load_halo(float *__restrict__ dst, const float *__restrict__ src, int x0, int y0, int W,
-                                          int H) {
-    constexpr int RW = kSsimHW * C;
-    for (int i = threadIdx.x; i < kSsimHH * RW; i += blockDim.x) {
-        const int r = i / RW, e = i - r * RW;
-        const int gy = y0 - kSsimR + r, gx = x0 - kSsimR + e / C;
-        dst[i] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? src[((int64_t)gy * W + gx) * C + (e % C)] : 0.f;
-    }
-}
-
 // One block per 32 x 16 tile, all three channels: the image and target halo
-// tiles are read once (interleaved, coalesced); per channel the five moments
-// are filtered (rows, then columns) and S, a, b, c formed.  abc: [H, W, 9]
-// (a, b, c of channel 0, then 1, then 2).
+// tiles are read once (interleaved, coalesced) into (x, y) pairs.  Per
+// channel, rows first: a thread filters 4 adjacent outputs of one halo row
+// from 14 inputs held in registers, the (x, y) and (x^2, y^2) moments as
+// f32x2 pairs; then columns: a thread filters 2 adjacent output rows of one
+// column from 12 staged rows.  S and the partials (a, b, c) per pixel and
+// channel are written interleaved, abc = [H, W, 9].
 __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *__restrict__ img, const float *__restrict__ tgt,
                                                        int W, int H, SsimWindow win, float *__restrict__ abc,
                                                        double *__restrict__ sums) {
-    __shared__ float xs[kSsimHH * kSsimHW * 3], ys[kSsimHH * kSsimHW * 3];
-    __shared__ float hs[5][kSsimHH][kSsimTW];
+    __shared__ float2 xy[3][kSsimHH][kSsimHW];           // (x, y) per channel
+    __shared__ float2 hm[2][kSsimHH][kSsimTW];           // filtered rows: (x, y), (x^2, y^2)
+    __shared__ float hc[kSsimHH][kSsimTW];               // filtered rows: x y
     __shared__ float red[2][8];
     const int x0 = blockIdx.x * kSsimTW, y0 = blockIdx.y * kSsimTH;
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-    load_halo<3>(xs, img, x0, y0, W, H);
-    load_halo<3>(ys, tgt, x0, y0, W, H);
+    for (int i = tid; i < kSsimHH * kSsimHW * 3; i += blockDim.x) {
+        const int r = i / (kSsimHW * 3), e = i - r * (kSsimHW * 3);
+        const int c = e / 3, ch = e - c * 3;
+        const int gy = y0 - kSsimR + r, gx = x0 - kSsimR + c;
+        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        const int64_t o = ((int64_t)gy * W + gx) * 3 + ch;
+        xy[ch][r][c] = make_float2(in ? img[o] : 0.f, in ? tgt[o] : 0.f);
+    }
     float s_sum = 0.f, l1_sum = 0.f;
     for (int ch = 0; ch < 3; ++ch) {
         __syncthreads();
-        for (int i = tid; i < kSsimHH * kSsimTW; i += blockDim.x) {
-            const int r = i / kSsimTW, c = i - r * kSsimTW;
-            const float *xr = xs + (r * kSsimHW + c) * 3 + ch, *yr = ys + (r * kSsimHW + c) * 3 + ch;
-            float sx = 0.f, sy = 0.f, sxx = 0.f, syy = 0.f, sxy = 0.f;
+        if (tid < kSsimHH * (kSsimTW / 4)) {  // 26 rows x 8 groups of 4 outputs
+            const int r = tid >> 3, c0 = (tid & 7) * 4;
+            float2 v[kSsimK + 3], v2[kSsimK + 3];
+            float vp[kSsimK + 3];
 #pragma unroll
-            for (int k = 0; k < kSsimK; ++k) {
-                const float w = win.w[k], xv = xr[3 * k], yv = yr[3 * k];
-                sx = fmaf(w, xv, sx);
-                sy = fmaf(w, yv, sy);
-                sxx = fmaf(w, xv * xv, sxx);
-                syy = fmaf(w, yv * yv, syy);
-                sxy = fmaf(w, xv * yv, sxy);
+            for (int j = 0; j < kSsimK + 3; ++j) {
+                v[j] = xy[ch][r][c0 + j];
+                v2[j] = __fmul2_rn(v[j], v[j]);
+                vp[j] = v[j].x * v[j].y;
             }
-            hs[0][r][c] = sx;
-            hs[1][r][c] = sy;
-            hs[2][r][c] = sxx;
-            hs[3][r][c] = syy;
-            hs[4][r][c] = sxy;
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                float2 m1 = make_float2(0.f, 0.f), m2 = m1;
+                float mp = 0.f;
+#pragma unroll
+                for (int k = 0; k < kSsimK; ++k) {
+                    const float2 wk = make_float2(win.w[k], win.w[k]);
+                    m1 = __ffma2_rn(wk, v[o + k], m1);
+                    m2 = __ffma2_rn(wk, v2[o + k], m2);
+                    mp = fmaf(win.w[k], vp[o + k], mp);
+                }
+                hm[0][r][c0 + o] = m1;
+                hm[1][r][c0 + o] = m2;
+                hc[r][c0 + o] = mp;
+            }
         }
         __syncthreads();
-        for (int rr = ty; rr < kSsimTH; rr += 8) {
-            const int gx = x0 + tx, gy = y0 + rr;
-            if (gx >= W || gy >= H) continue;
-            float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        {
+            const int rr0 = ty * 2;  // two output rows per thread: 8 x 2 = 16
+            float2 a1[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, a2[2] = {a1[0], a1[0]};
+            float ap[2] = {0.f, 0.f};
 #pragma unroll
-            for (int k = 0; k < kSsimK; ++k)
+            for (int j = 0; j < kSsimK + 1; ++j) {
+                const float2 h1 = hm[0][rr0 + j][tx], h2 = hm[1][rr0 + j][tx];
+                const float hp = hc[rr0 + j][tx];
 #pragma unroll
-                for (int q = 0; q < 5; ++q) m[q] = fmaf(win.w[k], hs[q][rr + k][tx], m[q]);
-            const float mx = m[0], my = m[1];
-            const float sxx = m[2] - mx * mx, syy = m[3] - my * my, sxy = m[4] - mx * my;
-            const float A = 2.f * mx * my + kSsimC1, B = 2.f * sxy + kSsimC2;
-            const float Cc = mx * mx + my * my + kSsimC1, D = sxx + syy + kSsimC2;
-            const float S = (A * B) / (Cc * D);
-            float *o = abc + ((int64_t)gy * W + gx) * 9 + 3 * ch;
-            o[0] = S * (2.f * my / A - 2.f * my / B - 2.f * mx / Cc + 2.f * mx / D);  // dS/dmu_x
-            o[1] = -S / D;                                                              // dS/dE[xx]
-            o[2] = 2.f * S / B;                                                         // dS/dE[xy]
-            s_sum += S;
-            const int ci = ((rr + kSsimR) * kSsimHW + tx + kSsimR) * 3 + ch;
-            l1_sum += fabsf(xs[ci] - ys[ci]);
+                for (int o = 0; o < 2; ++o) {
+                    const int k = j - o;
+                    if (k < 0 || k >= kSsimK) continue;
+                    const float2 wk = make_float2(win.w[k], win.w[k]);
+                    a1[o] = __ffma2_rn(wk, h1, a1[o]);
+                    a2[o] = __ffma2_rn(wk, h2, a2[o]);
+                    ap[o] = fmaf(win.w[k], hp, ap[o]);
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                const int gx = x0 + tx, gy = y0 + rr0 + o;
+                if (gx >= W || gy >= H) continue;
+                const float mx = a1[o].x, my = a1[o].y;
+                const float sxx = a2[o].x - mx * mx, syy = a2[o].y - my * my, sxy = ap[o] - mx * my;
+                const float A = 2.f * mx * my + kSsimC1, B = 2.f * sxy + kSsimC2;
+                const float Cc = mx * mx + my * my + kSsimC1, D = sxx + syy + kSsimC2;
+                const float S = (A * B) / (Cc * D);
+                float *out = abc + ((int64_t)gy * W + gx) * 9 + 3 * ch;
+                out[0] = S * (2.f * my / A - 2.f * my / B - 2.f * mx / Cc + 2.f * mx / D);  // dS/dmu_x
+                out[1] = -S / D;                                                              // dS/dE[xx]
+                out[2] = 2.f * S / B;                                                         // dS/dE[xy]
+                s_sum += S;
+                const float2 c = xy[ch][rr0 + o + kSsimR][tx + kSsimR];
+                l1_sum += fabsf(c.x - c.y);
+            }
         }
     }
 #pragma unroll
@@ -122,74 +140,108 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *__restrict__
 }
 
 // One block per 32 x 16 tile: per channel, the (a, b, c) halo tile is read
-// once (interleaved) and filtered; dL/dC per pixel, then the state rewrite.
+// once (interleaved) and filtered rows first (4 outputs per thread from 14
+// register-held inputs), then columns (2 output rows per thread); dL/dC per
+// pixel, then the state rewrite.
 __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *__restrict__ img, const float *__restrict__ tgt,
                                                        int W, int H, SsimWindow win, const float *__restrict__ abc,
                                                        float lambda, float bg0, float bg1, float bg2,
                                                        float *__restrict__ state, float *__restrict__ grad_out) {
-    __shared__ float ms[kSsimHH * kSsimHW * 3];
-    __shared__ float hs[9][kSsimHH][kSsimTW];
+    __shared__ float2 mab[kSsimHH][kSsimHW];       // (a, b) of one channel
+    __shared__ float mc[kSsimHH][kSsimHW];         // c of one channel
+    __shared__ float2 hab[3][kSsimHH][kSsimTW];    // filtered rows (a, b) per channel
+    __shared__ float hcc[3][kSsimHH][kSsimTW];     // filtered rows c per channel
     const int x0 = blockIdx.x * kSsimTW, y0 = blockIdx.y * kSsimTH;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
     const int64_t HW = (int64_t)W * H;
     for (int ch = 0; ch < 3; ++ch) {
         __syncthreads();
-        // the three partials of this channel: a halo of a [H, W, 9] array restricted to 3 values
-        for (int i = tid; i < kSsimHH * kSsimHW * 3; i += blockDim.x) {
-            const int r = i / (kSsimHW * 3), e = i - r * (kSsimHW * 3);
-            const int gy = y0 - kSsimR + r, gx = x0 - kSsimR + e / 3;
-            ms[i] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? abc[((int64_t)gy * W + gx) * 9 + 3 * ch + e % 3]
-                                                              : 0.f;
+        for (int i = tid; i < kSsimHH * kSsimHW; i += blockDim.x) {
+            const int r = i / kSsimHW, c = i - r * kSsimHW;
+            const int gy = y0 - kSsimR + r, gx = x0 - kSsimR + c;
+            float2 v = make_float2(0.f, 0.f);
+            float vc = 0.f;
+            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+                const float *p = abc + ((int64_t)gy * W + gx) * 9 + 3 * ch;
+                v = make_float2(p[0], p[1]);
+                vc = p[2];
+            }
+            mab[r][c] = v;
+            mc[r][c] = vc;
         }
         __syncthreads();
-        for (int i = tid; i < kSsimHH * kSsimTW; i += blockDim.x) {
-            const int r = i / kSsimTW, c = i - r * kSsimTW;
-            const float *mr = ms + (r * kSsimHW + c) * 3;
-            float fa = 0.f, fb = 0.f, fc = 0.f;
+        if (tid < kSsimHH * (kSsimTW / 4)) {
+            const int r = tid >> 3, c0 = (tid & 7) * 4;
+            float2 v[kSsimK + 3];
+            float vc[kSsimK + 3];
 #pragma unroll
-            for (int k = 0; k < kSsimK; ++k) {
-                fa = fmaf(win.w[k], mr[3 * k + 0], fa);
-                fb = fmaf(win.w[k], mr[3 * k + 1], fb);
-                fc = fmaf(win.w[k], mr[3 * k + 2], fc);
+            for (int j = 0; j < kSsimK + 3; ++j) {
+                v[j] = mab[r][c0 + j];
+                vc[j] = mc[r][c0 + j];
             }
-            hs[3 * ch + 0][r][c] = fa;
-            hs[3 * ch + 1][r][c] = fb;
-            hs[3 * ch + 2][r][c] = fc;
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                float2 ab = make_float2(0.f, 0.f);
+                float cc = 0.f;
+#pragma unroll
+                for (int k = 0; k < kSsimK; ++k) {
+                    ab = __ffma2_rn(make_float2(win.w[k], win.w[k]), v[o + k], ab);
+                    cc = fmaf(win.w[k], vc[o + k], cc);
+                }
+                hab[ch][r][c0 + o] = ab;
+                hcc[ch][r][c0 + o] = cc;
+            }
         }
     }
     __syncthreads();
-    const int tx = tid & 31, ty = tid >> 5;
     const float inv_n = 1.f / (3.f * (float)HW);
-    for (int rr = ty; rr < kSsimTH; rr += 8) {
-        const int gx = x0 + tx, gy = y0 + rr;
-        if (gx >= W || gy >= H) continue;
-        const int64_t pix = (int64_t)gy * W + gx;
-        float g[3];
+    const int rr0 = ty * 2;
+    float g[2][3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float fa = 0.f, fb = 0.f, fc = 0.f;
+    for (int c = 0; c < 3; ++c) {
+        float2 ab[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        float cc[2] = {0.f, 0.f};
 #pragma unroll
-            for (int k = 0; k < kSsimK; ++k) {
-                fa = fmaf(win.w[k], hs[3 * c + 0][rr + k][tx], fa);
-                fb = fmaf(win.w[k], hs[3 * c + 1][rr + k][tx], fb);
-                fc = fmaf(win.w[k], hs[3 * c + 2][rr + k][tx], fc);
+        for (int j = 0; j < kSsimK + 1; ++j) {
+            const float2 h = hab[c][rr0 + j][tx];
+            const float hz = hcc[c][rr0 + j][tx];
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                const int k = j - o;
+                if (k < 0 || k >= kSsimK) continue;
+                ab[o] = __ffma2_rn(make_float2(win.w[k], win.w[k]), h, ab[o]);
+                cc[o] = fmaf(win.w[k], hz, cc[o]);
             }
+        }
+#pragma unroll
+        for (int o = 0; o < 2; ++o) {
+            const int gx = x0 + tx, gy = y0 + rr0 + o;
+            g[o][c] = 0.f;
+            if (gx >= W || gy >= H) continue;
+            const int64_t pix = (int64_t)gy * W + gx;
             const float x = img[3 * pix + c], y = tgt[3 * pix + c];
-            const float dS = fa + 2.f * x * fb + y * fc;
+            const float dS = ab[o].x + 2.f * x * ab[o].y + y * cc[o];
             const float d = x - y;
             const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-            g[c] = ((1.f - lambda) * sg - lambda * dS) * inv_n;
-            if (grad_out) grad_out[3 * pix + c] = g[c];
+            g[o][c] = ((1.f - lambda) * sg - lambda * dS) * inv_n;
+            if (grad_out) grad_out[3 * pix + c] = g[o][c];
         }
+    }
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+        const int gx = x0 + tx, gy = y0 + rr0 + o;
+        if (gx >= W || gy >= H) continue;
+        const int64_t pix = (int64_t)gy * W + gx;
         // the forward left F (3), T, Q in the state planes; turn them into the backward state
         const float F0 = state[pix], F1 = state[HW + pix], F2 = state[2 * HW + pix];
         const float T = state[3 * HW + pix], Q = state[4 * HW + pix];
         const float Bq = Q > 0.f ? (1.f - T) / Q : 0.f;
-        state[pix] = Bq * g[0];
-        state[HW + pix] = Bq * g[1];
-        state[2 * HW + pix] = Bq * g[2];
-        state[3 * HW + pix] = T * (g[0] * (F0 - bg0) + g[1] * (F1 - bg1) + g[2] * (F2 - bg2));
-        state[4 * HW + pix] = -Bq * (g[0] * F0 + g[1] * F1 + g[2] * F2);
+        const float *gg = g[o];
+        state[pix] = Bq * gg[0];
+        state[HW + pix] = Bq * gg[1];
+        state[2 * HW + pix] = Bq * gg[2];
+        state[3 * HW + pix] = T * (gg[0] * (F0 - bg0) + gg[1] * (F1 - bg1) + gg[2] * (F2 - bg2));
+        state[4 * HW + pix] = -Bq * (gg[0] * F0 + gg[1] * F1 + gg[2] * F2);
     }
 }
 
