@@ -71,7 +71,7 @@ struct SsimLossArgs {
     double lambda;
     double inv_n[kMaxViews];  // 1 / (3 H W) per view
 };
-// One view: abc = [H, W, 9] floats (scratch), sums = 2 doubles (S, |x - y|), state = the view's
+// One view: abc = [3][H, W, 3] floats (scratch), sums = 2 doubles (S, |x - y|), state = the view's
 // five planes (F, T, Q in; the backward state out), grad_out = dL/dC [H, W, 3] or null.
 int launch_ssim_view(const float *img, const float *tgt, int W, int H, const SsimWindow &win, float *abc,
                      double *sums, float lambda, const float bg[3], float *state, float *grad_out, cudaStream_t st);

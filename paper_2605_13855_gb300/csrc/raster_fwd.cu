@@ -52,10 +52,13 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
     const int start = offsets[gt];
     const int end = (int)min((int64_t)offsets[gt + 1], cap);
 
-    float P0[kStrip], P1[kStrip], P2[kStrip], Q[kStrip], T[kStrip];
+    // per pixel: (P_r, P_g) and (P_b, Q) as f32x2 pairs (one paired FMA per pair of sums;
+    // each component rounds like the scalar FMA), T (log T in sums mode)
+    float2 P01[kStrip], P2Q[kStrip];
+    float T[kStrip];
 #pragma unroll
     for (int j = 0; j < kStrip; ++j) {
-        P0[j] = P1[j] = P2[j] = Q[j] = 0.f;
+        P01[j] = P2Q[j] = make_float2(0.f, 0.f);
         T[j] = kMode == kRasterSums ? 0.f : 1.f;  // log T in sums mode
     }
     unsigned n_contrib = 0;
@@ -101,9 +104,13 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
         __syncthreads();
         // two-level summation: 32-splat blocks into the total
         for (int jb = 0; jb < n; jb += 32) {
-        float b0[kStrip], b1[kStrip], b2[kStrip], bq[kStrip], bl[kStrip];
+        float2 b01[kStrip], b2q[kStrip];
+        float bl[kStrip];
 #pragma unroll
-        for (int j = 0; j < kStrip; ++j) b0[j] = b1[j] = b2[j] = bq[j] = bl[j] = 0.f;
+        for (int j = 0; j < kStrip; ++j) {
+            b01[j] = b2q[j] = make_float2(0.f, 0.f);
+            bl[j] = 0.f;
+        }
         const int je = min(n, jb + 32);
         for (int j = jb; j < je; ++j) {
             const float4 a0 = s0[j], a1 = s1[j];
@@ -114,10 +121,9 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
                 for (int p = 0; p < kStrip; ++p) {
                     const float sq = quad_s(col_e1(a0.w, rt.e10, sx + p), rt.e2sq);
                     const float a = fminf(fast_exp2(a1.z - sq), kAlphaMax);
-                    b0[p] = fmaf(a, a2.x, b0[p]);
-                    b1[p] = fmaf(a, a2.y, b1[p]);
-                    b2[p] = fmaf(a, a2.z, b2[p]);
-                    bq[p] = fmaf(a, a2.w, bq[p]);
+                    const float2 aa = make_float2(a, a);
+                    b01[p] = __ffma2_rn(aa, make_float2(a2.x, a2.y), b01[p]);
+                    b2q[p] = __ffma2_rn(aa, make_float2(a2.z, a2.w), b2q[p]);
                     if (kMode == kRasterSums)
                         bl[p] = fmaf(ssign[j], log1pf(-a), bl[p]);
                     else
@@ -137,10 +143,9 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
                 const float sq = quad_s(col_e1(a0.w, rt.e10, sx + p), rt.e2sq);
                 if (sq <= a1.y) {
                     const float a = fminf(fast_exp2(a1.z - sq), kAlphaMax);
-                    b0[p] = fmaf(a, a2.x, b0[p]);
-                    b1[p] = fmaf(a, a2.y, b1[p]);
-                    b2[p] = fmaf(a, a2.z, b2[p]);
-                    bq[p] = fmaf(a, a2.w, bq[p]);
+                    const float2 aa = make_float2(a, a);
+                    b01[p] = __ffma2_rn(aa, make_float2(a2.x, a2.y), b01[p]);
+                    b2q[p] = __ffma2_rn(aa, make_float2(a2.z, a2.w), b2q[p]);
                     if (kMode == kRasterSums)
                         bl[p] = fmaf(ssign[j], log1pf(-a), bl[p]);
                     else
@@ -151,10 +156,8 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
         }
 #pragma unroll
         for (int p = 0; p < kStrip; ++p) {
-            P0[p] += b0[p];
-            P1[p] += b1[p];
-            P2[p] += b2[p];
-            Q[p] += bq[p];
+            P01[p] = __fadd2_rn(P01[p], b01[p]);
+            P2Q[p] = __fadd2_rn(P2Q[p], b2q[p]);
             if (kMode == kRasterSums) T[p] += bl[p];
         }
         }
@@ -171,15 +174,15 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
         const int64_t pix = (int64_t)y * vd.W + x;
         if (kMode == kRasterSums) {
             float *fz = vd.frozen;
-            fz[pix] += P0[p];
-            fz[HW + pix] += P1[p];
-            fz[2 * HW + pix] += P2[p];
-            fz[3 * HW + pix] += Q[p];
+            fz[pix] += P01[p].x;
+            fz[HW + pix] += P01[p].y;
+            fz[2 * HW + pix] += P2Q[p].x;
+            fz[3 * HW + pix] += P2Q[p].y;
             fz[4 * HW + pix] += T[p];
         } else {
             const float *fz = vd.frozen;
-            const float Pt0 = P0[p] + fz[pix], Pt1 = P1[p] + fz[HW + pix], Pt2 = P2[p] + fz[2 * HW + pix];
-            const float Qt = Q[p] + fz[3 * HW + pix];
+            const float Pt0 = P01[p].x + fz[pix], Pt1 = P01[p].y + fz[HW + pix], Pt2 = P2Q[p].x + fz[2 * HW + pix];
+            const float Qt = P2Q[p].y + fz[3 * HW + pix];
             const float Tt = T[p] * expf(fz[4 * HW + pix]);
             const float invQ = Qt > 0.f ? 1.f / Qt : 0.f;
             const float F0 = Pt0 * invQ, F1 = Pt1 * invQ, F2 = Pt2 * invQ;

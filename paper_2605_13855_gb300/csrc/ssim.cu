@@ -13,7 +13,7 @@
 // Two passes per view, both on 32 x 16 output tiles with a 5-pixel halo held
 // in shared memory and the separable window applied rows first:
 //   ssim_fwd_kernel (all channels per block): the five filtered moments, S and
-//     (a, b, c) per pixel and channel, written interleaved [H, W, 9]; block
+//     (a, b, c) per pixel and channel, written as [3 channels][H, W, 3]; block
 //     sums of S and |x - y| into per-view doubles;
 //   ssim_bwd_kernel (all channels per block): filters (a, b, c), forms
 //     dL/dC and rewrites the forward's (F, T, Q) planes into the pixel state
@@ -33,7 +33,8 @@ constexpr float kSsimC1 = 0.01f * 0.01f, kSsimC2 = 0.03f * 0.03f;
 // from 14 inputs held in registers, the (x, y) and (x^2, y^2) moments as
 // f32x2 pairs; then columns: a thread filters 2 adjacent output rows of one
 // column from 12 staged rows.  S and the partials (a, b, c) per pixel and
-// channel are written interleaved, abc = [H, W, 9].
+// channel are written as abc = [3 channels][H, W, 3] (each channel's pass of
+// the backward then reads one contiguous array).
 __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *__restrict__ img, const float *__restrict__ tgt,
                                                        int W, int H, SsimWindow win, float *__restrict__ abc,
                                                        double *__restrict__ sums) {
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *__restrict__
                 const float A = 2.f * mx * my + kSsimC1, B = 2.f * sxy + kSsimC2;
                 const float Cc = mx * mx + my * my + kSsimC1, D = sxx + syy + kSsimC2;
                 const float S = (A * B) / (Cc * D);
-                float *out = abc + ((int64_t)gy * W + gx) * 9 + 3 * ch;
+                float *out = abc + (ch * (int64_t)W * H + (int64_t)gy * W + gx) * 3;
                 out[0] = S * (2.f * my / A - 2.f * my / B - 2.f * mx / Cc + 2.f * mx / D);  // dS/dmu_x
                 out[1] = -S / D;                                                              // dS/dE[xx]
                 out[2] = 2.f * S / B;                                                         // dS/dE[xy]
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *__restrict__
             float2 v = make_float2(0.f, 0.f);
             float vc = 0.f;
             if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-                const float *p = abc + ((int64_t)gy * W + gx) * 9 + 3 * ch;
+                const float *p = abc + (ch * HW + (int64_t)gy * W + gx) * 3;
                 v = make_float2(p[0], p[1]);
                 vc = p[2];
             }

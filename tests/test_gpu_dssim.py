@@ -70,3 +70,44 @@ def test_loss_needs_an_unfused_forward():
         r.loss_l1_dssim([target])
     r.backward(sp)
     r.status()
+
+
+def test_l1_dssim_over_a_batch_of_views():
+    """Two views of different sizes in one call: the loss is the sum of the per-view losses and the
+    gradients the sum of the per-view gradients."""
+    n = 15_000
+    scene = scenes.clustered_scene(n, 8300)
+    cams = [scenes.random_camera(8301, 90, 70), scenes.random_camera(8302, 53, 61)]
+    mask = scenes.random_active_mask(n, 0.2, 8303)
+    act = mask.astype(bool)
+    sp = R.SplatParams.from_numpy(scene)
+    r = R.Renderer(n, [(c["width"], c["height"]) for c in cams])
+    r.set_active(torch.as_tensor(mask, device="cuda"))
+    for v, c in enumerate(cams):
+        r.commit_frozen(sp, c, v, mode="recompute")
+    tg = []
+    refs = []
+    for k, c in enumerate(cams):
+        ref = oracle.render(scene, c, amb_band=AMB_BAND)
+        t = scenes.uniform_target(8310 + k, c["width"], c["height"]).astype(np.float64)
+        d = ref["image"] - t
+        t = np.where((np.abs(d) < 1e-4) & (d != 0), t - 1e-4 * np.sign(d), t).astype(np.float32)
+        tg.append(t)
+        refs.append(ref)
+    imgs, _ = r.forward(sp, cams, [0, 1])
+    loss = r.loss_l1_dssim([torch.as_tensor(t, device="cuda") for t in tg], 0.2)
+    grads = r.backward(sp)
+    r.status()
+    xs = [to_np(im) for im in imgs]
+    lref = sum(osm.loss_l1_dssim(x, t, 0.2) for x, t in zip(xs, tg))
+    assert abs(loss.item() - lref) <= 1e-5 * abs(lref)
+    total = None
+    for k, c in enumerate(cams):
+        rg = oracle_grads(scene, c, refs[k]["sums"], osm.grad_l1_dssim(xs[k], tg[k], 0.2), active=act)
+        if total is None:
+            total = rg
+        else:
+            for key in ("grads", "flip", "dsigma", "dsigma_scale", "dsigma_flip"):
+                total[key] = total[key] + rg[key]
+            total["amb"] = total["amb"] | rg["amb"]
+    check_against_oracle(grads, total, np.where(act)[0])
