@@ -263,12 +263,25 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(const int *__restrict_
     __syncthreads();
     for (int i = tid; i < total; i += 1024) atomicAdd(&cls_pos[load_class(count[i])], 1);
     __syncthreads();
-    if (tid == 0) {  // first position of each class, heaviest class first
-        int run = 0;
-        for (int k = kLoadClasses - 1; k >= 0; --k) {
-            const int h = cls_pos[k];
-            cls_pos[k] = run;
-            run += h;
+    if (warp == 0) {  // first position of each class, heaviest class first: a warp scan over
+                      // the classes in descending order, four per lane
+        int h[4], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            h[j] = cls_pos[kLoadClasses - 1 - (4 * lane + j)];
+            sum += h[j];
+        }
+        int incl = sum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        int run = incl - sum;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            cls_pos[kLoadClasses - 1 - (4 * lane + j)] = run;
+            run += h[j];
         }
     }
     __syncthreads();
