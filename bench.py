@@ -125,6 +125,13 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def _clock_dir() -> str:
+    """Where the nvidia-smi samples of the timed region are written (SPARSEOIT_CLOCKS_DIR, else the
+    system temporary directory)."""
+    import tempfile
+    return os.environ.get("SPARSEOIT_CLOCKS_DIR") or tempfile.gettempdir()
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -437,7 +444,7 @@ def run_active_update(args):
                                 mask=mask)
         stream.synchronize()
         times, fracs = [], []
-        with ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_active_update.csv")) as clk:
+        with ClockSampler(os.path.join(_clock_dir(), "clocks_active_update.csv")) as clk:
             for _ in range(args.steps):
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 first = int(rng.integers(V))
@@ -778,7 +785,7 @@ def main():
                     commit_recompute_ms=commit_ms, prof=prof, out=out, mask=mask)
 
     results = {}
-    clock_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+    clock_path = os.path.join(_clock_dir(), f"clocks_rank{rank}.csv")
     os.makedirs(os.path.dirname(clock_path), exist_ok=True)
     fr_list = [HEADLINE_FRACTION, 1.0] if args.no_sweep else list(FRACTIONS)
     if args.fractions:

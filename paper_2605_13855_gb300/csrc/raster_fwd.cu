@@ -24,6 +24,31 @@ namespace soit {
 
 constexpr int kFwdBatch = 256;    // records staged per round
 
+// The strip's quadratics s = e1^2 + e2^2 and log2 alpha_raw = log2 o - s, two
+// pixels per f32x2 instruction where the strip has pairs (each component
+// rounds like the scalar FMA, so the decisions match the backward's).
+template <int kStrip>
+__device__ __forceinline__ void strip_exponents(float A2, float e10, float e2sq, float log2o, int sx, float *sq,
+                                                float *lg) {
+    if (kStrip == 1) {
+        sq[0] = quad_s(col_e1(A2, e10, sx), e2sq);
+        lg[0] = log2o - sq[0];
+    } else {
+        const float2 A2p = make_float2(A2, A2), e10p = make_float2(e10, e10), e2p = make_float2(e2sq, e2sq);
+        const float2 l2p = make_float2(log2o, log2o), m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+        for (int p = 0; p < kStrip; p += 2) {
+            const float2 e1 = __ffma2_rn(A2p, make_float2((float)(sx + p), (float)(sx + p + 1)), e10p);
+            const float2 q = __ffma2_rn(e1, e1, e2p);
+            const float2 l = __ffma2_rn(q, m1, l2p);  // -s + log2 o: one rounding, as the subtraction
+            sq[p] = q.x;
+            sq[p + 1] = q.y;
+            lg[p] = l.x;
+            lg[p + 1] = l.y;
+        }
+    }
+}
+
 template <int kMode, bool kCount, int kStrip>
 __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip == 2 ? 4 : 8)) raster_fwd_kernel(const __grid_constant__ Batch b,
                                                                  const float4 *__restrict__ rec,
@@ -117,10 +142,11 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
             if (sfl[j]) {  // block-uniform: every pixel of the tile contributes, no cutoff test
                 const RowTerms rt = row_terms(a0.x, a0.y, a0.z, a1.x, ky);
                 const float4 a2 = s2[j];
+                float sq[kStrip], lg[kStrip];
+                strip_exponents<kStrip>(a0.w, rt.e10, rt.e2sq, a1.z, sx, sq, lg);
 #pragma unroll
                 for (int p = 0; p < kStrip; ++p) {
-                    const float sq = quad_s(col_e1(a0.w, rt.e10, sx + p), rt.e2sq);
-                    const float a = fminf(fast_exp2(a1.z - sq), kAlphaMax);
+                    const float a = fminf(fast_exp2(lg[p]), kAlphaMax);
                     const float2 aa = make_float2(a, a);
                     b01[p] = __ffma2_rn(aa, make_float2(a2.x, a2.y), b01[p]);
                     b2q[p] = __ffma2_rn(aa, make_float2(a2.z, a2.w), b2q[p]);
@@ -138,11 +164,12 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
             const RowTerms rt = row_terms(a0.x, a0.y, a0.z, a1.x, ky);
             if (rt.e2sq > a1.y) continue;  // whole row outside (s >= e2^2 for every pixel of it)
             const float4 a2 = s2[j];
+            float sq[kStrip], lg[kStrip];
+            strip_exponents<kStrip>(a0.w, rt.e10, rt.e2sq, a1.z, sx, sq, lg);
 #pragma unroll
             for (int p = 0; p < kStrip; ++p) {
-                const float sq = quad_s(col_e1(a0.w, rt.e10, sx + p), rt.e2sq);
-                if (sq <= a1.y) {
-                    const float a = fminf(fast_exp2(a1.z - sq), kAlphaMax);
+                if (sq[p] <= a1.y) {
+                    const float a = fminf(fast_exp2(lg[p]), kAlphaMax);
                     const float2 aa = make_float2(a, a);
                     b01[p] = __ffma2_rn(aa, make_float2(a2.x, a2.y), b01[p]);
                     b2q[p] = __ffma2_rn(aa, make_float2(a2.z, a2.w), b2q[p]);
