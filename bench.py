@@ -982,6 +982,12 @@ def main():
                         "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (sm_max_mhz of "
                                        f"MEASURED_PEAKS.json, {peak_kind})",
                         "algorithmic": f"E={head['E']} pairs x {FLOPS_BWD_PER_EVAL if dom == 'raster_bwd' else FLOPS_FWD_PER_EVAL} FP32 ops"}
+    # FP32 issue-bound rasters: achieved flops of both against the FP32 peak
+    fp32 = {}
+    for k, per in (("raster_fwd", FLOPS_FWD_PER_EVAL), ("raster_bwd", FLOPS_BWD_PER_EVAL)):
+        if k in per_kernel and per_kernel[k]["avg_ms"] > 0:
+            ach = head["E"] * per / (per_kernel[k]["avg_ms"] * 1e-3) / 1e12
+            fp32[k] = {"achieved_tflops": ach, "frac": ach / peak_tf, "flops_per_pair": per}
     gpu_launches = 6 * args.steps  # project, scan, scatter, raster_fwd, raster_bwd, project_bwd
     n_tiles = ((W + 15) // 16) * ((H + 15) // 16)
     hbm = hbm_report(per_kernel, head["n_active"], head["M"], W * H, n_tiles, ms, peaks, peak_kind)
@@ -1012,6 +1018,7 @@ def main():
         "stage_update": {"set_active_ms": set_active_ms, "commit_incremental_ms": commit_inc_ms},
         "per_kernel_ms": per_kernel,
         "roofline": roofline,
+        "fp32": {"peak_tflops": peak_tf, "per_kernel": fp32},
         "train_iteration_with_sparse_adam": train,
         "step_with_l1_dssim_loss": dssim,
         "evals_tile_per_s": 256 * head["M"] / (ms * 1e-3),
