@@ -443,6 +443,26 @@ def run_active_update(args):
             r.update_active_set(sp, cams, targets, eps, S, int(rng.integers(V)), stream=stream, scratch=scratch,
                                 mask=mask)
         stream.synchronize()
+        # the delayed frozen-sum updates of a stage: every view committed under the current set, then
+        # one more update, then every view brought up to date incrementally (against a recompute)
+        for v in range(V):
+            r.commit_frozen(sp, cams[v], v, mode="recompute", stream=stream)
+        r.update_active_set(sp, cams, targets, eps, S, int(rng.integers(V)), stream=stream, scratch=scratch,
+                            mask=mask)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for v in range(V):
+            r.commit_frozen(sp, cams[v], v, mode="incremental", stream=stream)
+        b.record(stream)
+        stream.synchronize()
+        commit_inc_ms = a.elapsed_time(b)
+        r.set_active(mask, stream=stream)  # the same set again: every view stale, recompute timed
+        a.record(stream)
+        for v in range(V):
+            r.commit_frozen(sp, cams[v], v, mode="recompute", stream=stream)
+        b.record(stream)
+        stream.synchronize()
+        commit_rec_ms = a.elapsed_time(b)
         times, fracs = [], []
         with ClockSampler(os.path.join(_clock_dir(), "clocks_active_update.csv")) as clk:
             for _ in range(args.steps):
@@ -465,7 +485,9 @@ def run_active_update(args):
                                    "farthest point sampling, fused L1, thresholds = 99th percentile of each group's "
                                    "nonzero norms", "l2": "inputs (60 x 13 MB targets, 300 MB gradients) exceed L2"},
             "ms_per_subsampled_view": ms / S, "active_fraction_after": float(np.mean(fracs)), "eps": eps,
-            "amortised_ms_per_iteration_at_interval_500": ms / 500.0, "clocks": clocks}
+            "amortised_ms_per_iteration_at_interval_500": ms / 500.0,
+            "commit_all_views_after_update_ms": {"incremental": commit_inc_ms, "recompute": commit_rec_ms},
+            "stage_overhead_ms_per_iteration_at_interval_500": (ms + commit_inc_ms) / 500.0, "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 

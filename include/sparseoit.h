@@ -305,18 +305,20 @@ int sparseoit_activeness(const sparseoit_grads *g, int64_t n, const float *eps, 
 
 /* The whole periodic active-set update of Alg. 1 on the context: picks
  * n_sub of the n_views training views by sparseoit_fps_views (from
- * `first`), makes every splat active, and for each picked view j commits
- * its (empty) complement, renders the full set with the fused L1 loss
- * against d_targets[j] (device FP32 [H_j, W_j, 3]) and back-propagates,
- * summing the gradients of the n_sub view losses into `scratch` (full rows
- * indexed by splat, device FP32, overwritten; scratch->sigma receives the
- * summed dL/dsigma).  Then sparseoit_activeness(scratch, eps) writes the new
- * mask to d_mask (device u8[max_splats]) and the call ends with
- * sparseoit_set_active(d_mask): every view's frozen sums are stale
- * afterwards and are recommitted when next used (the delayed update of
- * Sec. 4.1).  cams: host [n_views], the context's views in order (view k
- * has the context's size k); sel_out: host int32 [n_sub] (nullable)
- * receives the picked views.  Synchronises `stream` (set_active does). */
+ * `first`); for each picked view j renders the whole splat set (every
+ * splat, no frozen sums) with the fused L1 loss against d_targets[j]
+ * (device FP32 [H_j, W_j, 3]) and back-propagates, summing the gradients of
+ * the n_sub view losses into `scratch` (full rows indexed by splat, device
+ * FP32, overwritten; scratch->sigma receives the summed dL/dsigma).  The
+ * current active set and the views' frozen sums are not touched by these
+ * renders.  Then sparseoit_activeness(scratch, eps) writes the new mask to
+ * d_mask (device u8[max_splats]) and the call ends with
+ * sparseoit_set_active(d_mask): every view is stale afterwards, and a view
+ * committed under the previous active set is brought up to date by an
+ * INCREMENTAL commit of the changes (the delayed update of Sec. 4.1).
+ * cams: host [n_views], the context's views in order (view k has the
+ * context's size k); sel_out: host int32 [n_sub] (nullable) receives the
+ * picked views.  Synchronises `stream` (set_active does). */
 int sparseoit_update_active_set(sparseoit_ctx *ctx, const sparseoit_splats *splats, const sparseoit_camera *cams,
                                 int32_t n_views, const float *const *d_targets, int32_t n_sub, int32_t first,
                                 const float *eps, sparseoit_grads *scratch, uint8_t *d_mask, int32_t *sel_out,

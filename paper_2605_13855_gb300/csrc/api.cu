@@ -73,6 +73,8 @@ struct sparseoit_ctx {
     bool last_fused = false;
     Batch last_batch;
     int last_n_list = 0;
+    const int *last_list = nullptr;  // index list of the last forward (active list or identity)
+    int *d_idx_all = nullptr;        // identity list 0..N-1 (full-set renders of the active-set update)
     int64_t last_generation = -1;
 };
 
@@ -358,7 +360,8 @@ int sparseoit_destroy(sparseoit_ctx *ctx) {
     void *bufs[] = {ctx->d_mask[0], ctx->d_mask[1], ctx->d_idx_active, ctx->d_idx_comp, ctx->d_idx_plus,
                     ctx->d_idx_minus, ctx->d_blk, ctx->d_totals, ctx->d_rec, ctx->d_ext, ctx->d_tile_count,
                     ctx->d_offsets, ctx->d_cursor, ctx->d_order, ctx->d_pairs, ctx->d_sgrad, ctx->d_status, ctx->d_npairs,
-                    ctx->d_contrib, ctx->d_upd_image, ctx->d_upd_loss, ctx->d_ssim_abc, ctx->d_ssim_sums};
+                    ctx->d_contrib, ctx->d_upd_image, ctx->d_upd_loss, ctx->d_ssim_abc, ctx->d_ssim_sums,
+                    ctx->d_idx_all};
     for (void *p : bufs) if (p) cudaFree(p);
     if (ctx->h_totals) cudaFreeHost(ctx->h_totals);
     for (auto &m : ctx->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
@@ -453,17 +456,33 @@ int sparseoit_commit_frozen(sparseoit_ctx *ctx, const sparseoit_splats *splats, 
     return SPARSEOIT_OK;
 }
 
-int sparseoit_forward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const sparseoit_camera *cams,
-                      const int32_t *views, int32_t n_views, float *const *d_images, const float *const *d_targets,
-                      float *d_loss, void *stream) {
+// The forward over an index list: the context's active list composed with each view's frozen sums,
+// or (whole_set) every splat of the scene with no frozen sums -- the full-set render of the
+// active-set update, which leaves the active set and the frozen sums as they are.
+static int forward_impl(sparseoit_ctx *ctx, const sparseoit_splats *splats, const sparseoit_camera *cams,
+                        const int32_t *views, int32_t n_views, float *const *d_images, const float *const *d_targets,
+                        float *d_loss, void *stream, bool whole_set) {
     if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
-    int rc = check_splats(ctx, splats, true);
+    int rc = check_splats(ctx, splats, !whole_set);
     if (rc) return rc;
-    if (!ctx->have_mask) return fail(ctx, SPARSEOIT_ERR_STATE, "forward before set_active");
+    if (!whole_set && !ctx->have_mask) return fail(ctx, SPARSEOIT_ERR_STATE, "forward before set_active");
     if (n_views < 1 || n_views > kMaxViews || !cams || !views || !d_images)
         return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "bad view list");
     if (d_targets && !d_loss) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "targets given without a loss pointer");
     cudaStream_t st = (cudaStream_t)stream;
+    const int *list = ctx->d_idx_active;
+    int64_t n_list = ctx->n_active;
+    if (whole_set) {
+        if (!ctx->d_idx_all) {
+            std::vector<int> iota((size_t)ctx->N);
+            for (int64_t i = 0; i < ctx->N; ++i) iota[(size_t)i] = (int)i;
+            CK(cudaMalloc((void **)&ctx->d_idx_all, (size_t)ctx->N * sizeof(int)), "cudaMalloc(identity list)");
+            CK(cudaMemcpy(ctx->d_idx_all, iota.data(), (size_t)ctx->N * sizeof(int), cudaMemcpyHostToDevice),
+               "copy(identity list)");
+        }
+        list = ctx->d_idx_all;
+        n_list = ctx->N;
+    }
     Batch b;
     memset(&b, 0, sizeof(b));
     b.n_views = n_views;
@@ -473,11 +492,12 @@ int sparseoit_forward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const 
         if (v < 0 || v >= ctx->n_views) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "view index out of range");
         for (int j = 0; j < k; ++j)
             if (views[j] == v) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "a view is listed twice");
-        if (ctx->view_gen[v] != ctx->generation)
+        if (!whole_set && ctx->view_gen[v] != ctx->generation)
             return fail(ctx, SPARSEOIT_ERR_STATE, "frozen sums of view " + std::to_string(v) +
                                                       " are stale: call sparseoit_commit_frozen first");
         rc = fill_view(ctx, &cams[k], v, b.v[k], tiles);
         if (rc) return rc;
+        if (whole_set) b.v[k].frozen = nullptr;
         if (!d_images[k]) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "image pointer is null");
         b.v[k].image = d_images[k];
         if (d_targets) {
@@ -487,18 +507,18 @@ int sparseoit_forward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const 
         tiles += b.v[k].tiles_x * b.v[k].tiles_y;
     }
     b.total_tiles = tiles;
-    b.n_list = (int)ctx->n_active;
+    b.n_list = (int)n_list;
     while ((int)ctx->d_state.size() < n_views) ctx->d_state.push_back(nullptr);
     for (int k = 0; k < n_views; ++k) {
         if (!ctx->d_state[k]) CK(cudaMalloc((void **)&ctx->d_state[k], (size_t)(5 * ctx->max_pix) * sizeof(float)),
                                  "cudaMalloc(pixel state)");
         b.v[k].state = ctx->d_state[k];
     }
-    rc = ensure_batch_ws(ctx, (int64_t)n_views * ctx->n_active, tiles);
+    rc = ensure_batch_ws(ctx, (int64_t)n_views * n_list, tiles);
     if (rc) return rc;
     if (d_loss) CK(cudaMemsetAsync(d_loss, 0, sizeof(float), st), "memset(loss)");
     if (ctx->counting) CK(cudaMemsetAsync(ctx->d_contrib, 0, sizeof(unsigned long long), st), "memset(counter)");
-    rc = render_pass_bin(ctx, b, splats, ctx->d_idx_active, (int)ctx->n_active, nullptr, 0, st);
+    rc = render_pass_bin(ctx, b, splats, list, (int)n_list, nullptr, 0, st);
     if (rc) return rc;
     {
         ProfScope ps(ctx, "raster_fwd", st);
@@ -510,9 +530,16 @@ int sparseoit_forward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const 
     ctx->have_fwd = true;
     ctx->last_fused = d_targets != nullptr;
     ctx->last_batch = b;
-    ctx->last_n_list = (int)ctx->n_active;
+    ctx->last_list = list;
+    ctx->last_n_list = (int)n_list;
     ctx->last_generation = ctx->generation;
     return SPARSEOIT_OK;
+}
+
+int sparseoit_forward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const sparseoit_camera *cams,
+                      const int32_t *views, int32_t n_views, float *const *d_images, const float *const *d_targets,
+                      float *d_loss, void *stream) {
+    return forward_impl(ctx, splats, cams, views, n_views, d_images, d_targets, d_loss, stream, false);
 }
 
 int sparseoit_backward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const float *const *d_grad_images,
@@ -522,6 +549,8 @@ int sparseoit_backward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const
     if (rc) return rc;
     if (!ctx->have_fwd || ctx->last_generation != ctx->generation)
         return fail(ctx, SPARSEOIT_ERR_STATE, "backward without a matching forward");
+    if (splats->rows == SPARSEOIT_ROWS_ACTIVE && ctx->last_list != ctx->d_idx_active)
+        return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "active rows after a full-set forward");
     if (!out || !out->means || !out->quats || !out->log_scales || !out->opacity_logits || !out->sh_color ||
         !out->sh_weight || !out->sigma)
         return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "a gradient pointer is null");
@@ -558,7 +587,7 @@ int sparseoit_backward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const
                out->accumulate != 0};
     {
         ProfScope ps(ctx, "project_bwd", st);
-        launch_project_bwd(b, splat_ptrs(splats), splats->sh_dtype == SPARSEOIT_BF16, ctx->d_idx_active,
+        launch_project_bwd(b, splat_ptrs(splats), splats->sh_dtype == SPARSEOIT_BF16, ctx->last_list,
                            ctx->last_n_list, ctx->d_sgrad, g, st);
     }
     CK_LAUNCH("project_bwd_kernel");
@@ -583,18 +612,14 @@ int sparseoit_update_active_set(sparseoit_ctx *ctx, const sparseoit_splats *spla
         CK(cudaMalloc((void **)&ctx->d_upd_image, (size_t)(3 * ctx->max_pix) * sizeof(float)), "cudaMalloc(update image)");
         CK(cudaMalloc((void **)&ctx->d_upd_loss, sizeof(float)), "cudaMalloc(update loss)");
     }
-    // every splat active: the full-set render of Alg. 1 (the complement is empty)
-    CK(cudaMemsetAsync(d_mask, 1, (size_t)ctx->N, st), "memset(mask)");
-    rc = sparseoit_set_active(ctx, d_mask, ctx->N, stream);
-    if (rc) return rc;
+    // the full-set render of Alg. 1: every splat, no frozen sums, the current active set and the
+    // views' frozen sums left as they are (so the commits after the update are incremental)
     sparseoit_grads g = *scratch;
     g.rows_by_splat = 1;
     for (int k = 0; k < n_sub; ++k) {
         const int32_t j = sel[k];
-        rc = sparseoit_commit_frozen(ctx, splats, &cams[j], j, SPARSEOIT_COMMIT_RECOMPUTE, stream);
-        if (rc) return rc;
         float *img = ctx->d_upd_image;
-        rc = sparseoit_forward(ctx, splats, &cams[j], &j, 1, &img, &d_targets[j], ctx->d_upd_loss, stream);
+        rc = forward_impl(ctx, splats, &cams[j], &j, 1, &img, &d_targets[j], ctx->d_upd_loss, stream, true);
         if (rc) return rc;
         g.accumulate = k > 0 ? 1 : 0;  // the gradient of the sum of the subsampled views' losses
         rc = sparseoit_backward(ctx, splats, nullptr, &g, stream);

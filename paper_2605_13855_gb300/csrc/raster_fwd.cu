@@ -207,10 +207,13 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
             fz[3 * HW + pix] += P2Q[p].y;
             fz[4 * HW + pix] += T[p];
         } else {
+            // the frozen complement's sums (none when the whole set is rendered)
             const float *fz = vd.frozen;
-            const float Pt0 = P01[p].x + fz[pix], Pt1 = P01[p].y + fz[HW + pix], Pt2 = P2Q[p].x + fz[2 * HW + pix];
-            const float Qt = P2Q[p].y + fz[3 * HW + pix];
-            const float Tt = T[p] * expf(fz[4 * HW + pix]);
+            const float f0 = fz ? fz[pix] : 0.f, f1 = fz ? fz[HW + pix] : 0.f, f2 = fz ? fz[2 * HW + pix] : 0.f;
+            const float fq = fz ? fz[3 * HW + pix] : 0.f;
+            const float Pt0 = P01[p].x + f0, Pt1 = P01[p].y + f1, Pt2 = P2Q[p].x + f2;
+            const float Qt = P2Q[p].y + fq;
+            const float Tt = fz ? T[p] * expf(fz[4 * HW + pix]) : T[p];
             const float invQ = Qt > 0.f ? 1.f / Qt : 0.f;
             const float F0 = Pt0 * invQ, F1 = Pt1 * invQ, F2 = Pt2 * invQ;
             const float omT = 1.f - Tt;

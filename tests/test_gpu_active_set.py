@@ -70,7 +70,9 @@ def test_update_active_set_matches_oracle():
 
     sp = R.SplatParams.from_numpy(scene)
     r = R.Renderer(n, [(cm["width"], cm["height"]) for cm in cams])
-    r.set_active(torch.zeros(n, dtype=torch.uint8, device="cuda"))  # a previous active set (empty)
+    prev = scenes.random_active_mask(n, 0.3, 7400)  # a previous active set, view 0 committed under it
+    r.set_active(torch.as_tensor(prev, device="cuda"))
+    r.commit_frozen(sp, cams[0], 0, mode="recompute")
     tg = [torch.as_tensor(t, device="cuda") for t in targets]
     mask, sel, grads = r.update_active_set(sp, cams, tg, eps, n_sub, first)
     r.status()
@@ -101,6 +103,15 @@ def test_update_active_set_matches_oracle():
     assert torch.equal(r.active_indices().cpu(), torch.as_tensor(np.where(m)[0], dtype=torch.int32))
     with pytest.raises(R.SparseOITError):
         r.forward(sp, [cams[0]], [0])
-    r.commit_frozen(sp, cams[0], 0)
+    # the update left view 0's frozen sums as they were: the incremental commit (+D+ -D- against the
+    # previous set) gives the new complement's sums, equal to a recompute and to the oracle
+    r.commit_frozen(sp, cams[0], 0, mode="incremental")
+    inc = to_np(r.frozen_sums(0))
+    ab = np.zeros((3, cams[0]["height"], cams[0]["width"]))
+    fz_ref, _, _ = oracle.render_sums(scene, cams[0], subset=~m.astype(bool), amb_band=AMB_BAND, amb_sums=ab)
+    # allowance of the near-cut pairs per plane: sum a w max c (P), sum a w (Q), sum a/(1-a) (log T)
+    allow = [ab[2], ab[2], ab[2], ab[1], ab[0]]
+    for k in range(5):
+        assert np.max(np.abs(inc[k] - fz_ref[k]) - allow[k]) <= 1e-5 * np.abs(fz_ref[k]).max(), k
     r.forward(sp, [cams[0]], [0])
     r.status()
