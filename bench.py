@@ -381,6 +381,14 @@ def run_batched(args):
             r.backward(sp, stream=stream, out=out)
 
         res["autotuned_ms"] = _graph_time(torch, stream, flush, batched_step, args.steps, args.warmup)
+        rA.set_profiling(True)
+        rA.get_profile()
+        for _ in range(args.steps):
+            flush.zero_()
+            batched_step()
+        stream.synchronize()
+        res["per_kernel_ms"] = {k: v[1] / max(1, v[0]) for k, v in rA.get_profile().items()}
+        rA.set_profiling(False)
 
         def separate_step():
             for k in views:
@@ -407,7 +415,8 @@ def run_batched(args):
                        "evals_per_step": E, "pairs_per_step": M, "n_active": int(mask.sum().item())},
             "variants_ms": {"autotuned_one_call": ms, "fixed_1px_per_thread_one_call": res["fixed_1px_ms"],
                             "16_separate_calls": res["separate_calls_ms"]},
-            "autotune": tune, "commit_recompute_16_views_ms": res["commit_recompute_16_views_ms"]}
+            "autotune": tune, "commit_recompute_16_views_ms": res["commit_recompute_16_views_ms"],
+            "per_kernel_ms": res["per_kernel_ms"]}
     print(json.dumps(line), flush=True)
 
 

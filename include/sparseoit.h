@@ -109,7 +109,7 @@ typedef struct {
     int64_t n;                    /* number of rows (max_splats, or |A| for ROWS_ACTIVE) */
     int32_t rows;                 /* SPARSEOIT_ROWS_BY_SPLAT or SPARSEOIT_ROWS_ACTIVE */
     int32_t reserved;
-} sparseoit_splats;
+} sparseoit_splats;               /* quats, sh_color and sh_weight 16-byte aligned (vector loads) */
 
 /* Gradient outputs, device pointers.  Only active splats receive gradients
  * (Sec. 4.1).  With rows_by_splat == 0 the rows are COMPACT: row r belongs to

@@ -157,8 +157,8 @@ static int check_splats(sparseoit_ctx *ctx, const sparseoit_splats *s, bool allo
     }
     if (!s->means || !s->quats || !s->log_scales || !s->opacity_logits || !s->sh_color || !s->sh_weight)
         return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "a splat parameter pointer is null");
-    if (((uintptr_t)s->quats & 15u) != 0)
-        return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "quats must be 16-byte aligned");
+    if (((uintptr_t)s->quats & 15u) != 0 || ((uintptr_t)s->sh_color & 15u) != 0 || ((uintptr_t)s->sh_weight & 15u) != 0)
+        return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "quats, sh_color and sh_weight must be 16-byte aligned");
     if (s->sh_dtype != SPARSEOIT_F32 && s->sh_dtype != SPARSEOIT_BF16)
         return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "unknown sh_dtype");
     if (!(s->sigma > 0.f)) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "sigma must be > 0");

@@ -158,20 +158,52 @@ __device__ __forceinline__ void sh_grad16(float x, float y, float z, const float
     g[0] = gx; g[1] = gy; g[2] = gz;
 }
 
-// Cooperative SH evaluation by a group of G lanes (G = 4 or 16; lane k of the
-// group holds coefficients k, k + G, ...): the basis value of coefficient
-// k + G j for this lane, picked without dynamic register indexing.
+// Cooperative SH evaluation by a group of G lanes (G = 1, 2, 4 or 16): lane
+// k of the group holds the J = 16 / G consecutive coefficients J k, ...,
+// J k + J - 1 (one contiguous run of the splat's row, loaded as vectors);
+// yk[j] is the basis value of coefficient J k + j, picked without dynamic
+// register indexing.
 template <int G>
 __device__ __forceinline__ void sh_basis_group(float x, float y, float z, int k, float yk[16 / G]) {
+    constexpr int J = 16 / G;
     float Y[16];
     sh_basis16(x, y, z, Y);
 #pragma unroll
-    for (int j = 0; j < 16 / G; ++j) {
-        float v = Y[G * j];
+    for (int j = 0; j < J; ++j) {
+        float v = Y[j];
 #pragma unroll
-        for (int m = 1; m < G; ++m) v = (k == m) ? Y[G * j + m] : v;
+        for (int m = 1; m < G; ++m) v = (k == m) ? Y[J * m + j] : v;
         yk[j] = v;
     }
+}
+
+// The J consecutive colour (3 per coefficient) and weight coefficients from
+// coefficient c0 of one splat's rows hc [16, 3] and hw [16]: 16-byte vector
+// loads for FP32 with J = 4 (rows are 192 and 64 bytes, so every run is
+// 16-byte aligned), scalar loads otherwise.
+template <typename T, int J>
+__device__ __forceinline__ void load_sh_run(const T *hc, const T *hw, int c0, float h0[J], float h1[J], float h2[J],
+                                            float hv[J]) {
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        h0[j] = ldf(hc, 3 * (c0 + j) + 0);
+        h1[j] = ldf(hc, 3 * (c0 + j) + 1);
+        h2[j] = ldf(hc, 3 * (c0 + j) + 2);
+        hv[j] = ldf(hw, c0 + j);
+    }
+}
+template <>
+__device__ __forceinline__ void load_sh_run<float, 4>(const float *hc, const float *hw, int c0, float h0[4],
+                                                      float h1[4], float h2[4], float hv[4]) {
+    const float4 *c4 = reinterpret_cast<const float4 *>(hc + 3 * c0);
+    const float4 a = __ldg(c4), b = __ldg(c4 + 1), c = __ldg(c4 + 2);
+    // (r0 g0 b0 r1) (g1 b1 r2 g2) (b2 r3 g3 b3)
+    h0[0] = a.x; h1[0] = a.y; h2[0] = a.z;
+    h0[1] = a.w; h1[1] = b.x; h2[1] = b.y;
+    h0[2] = b.z; h1[2] = b.w; h2[2] = c.x;
+    h0[3] = c.y; h1[3] = c.z; h2[3] = c.w;
+    const float4 w = __ldg(reinterpret_cast<const float4 *>(hw + c0));
+    hv[0] = w.x; hv[1] = w.y; hv[2] = w.z; hv[3] = w.w;
 }
 
 // Mask of the G lanes of this lane's group (groups are aligned in the warp).

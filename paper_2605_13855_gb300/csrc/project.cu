@@ -65,9 +65,10 @@ __device__ __forceinline__ bool row_tiles(const ViewDesc &vd, float mx, float my
     return true;
 }
 
-// G lanes (G = 4 or 16) per list entry r, looping over the views of the
+// G lanes (G = 1, 2, 4 or 16) per list entry r, looping over the views of the
 // batch so that the splat's parameters are read from HBM once.  Lane k of the
-// group loads SH coefficients k, k + G, ... (a coalesced row per splat), the
+// group loads the SH coefficients J k .. J k + J - 1 (J = 16 / G; one
+// contiguous run, vector loads; the group reads the whole row), the
 // lanes evaluate their basis values and sum the products with shuffles; the
 // geometry is evaluated redundantly by the G lanes; the tile rows of the
 // cutoff ellipse are counted by the lanes in parallel.  List entry r < n1 is
@@ -97,14 +98,7 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Ba
     const ShT *hc = reinterpret_cast<const ShT *>(sp.sh_color) + 48 * (int64_t)i;
     const ShT *hw = reinterpret_cast<const ShT *>(sp.sh_weight) + 16 * (int64_t)i;
     float h0[J], h1[J], h2[J], hv[J];
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-        const int kk = k + G * j;
-        h0[j] = ldf(hc, 3 * kk + 0);
-        h1[j] = ldf(hc, 3 * kk + 1);
-        h2[j] = ldf(hc, 3 * kk + 2);
-        hv[j] = ldf(hw, kk);
-    }
+    load_sh_run<ShT, J>(hc, hw, J * k, h0, h1, h2, hv);
 
     for (int v = 0; v < b.n_views; ++v) {
         const ViewDesc &vd = b.v[v];

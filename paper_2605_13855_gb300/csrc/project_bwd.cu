@@ -106,11 +106,17 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(const __grid_constant_
             sh_basis16(nx, ny, nz, Y);
             float craw[3] = {0.5f, 0.5f, 0.5f}, vraw = 0.5f;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                craw[0] = fmaf(Y[k], ldf(hc, 3 * k + 0), craw[0]);
-                craw[1] = fmaf(Y[k], ldf(hc, 3 * k + 1), craw[1]);
-                craw[2] = fmaf(Y[k], ldf(hc, 3 * k + 2), craw[2]);
-                vraw = fmaf(Y[k], ldf(hw, k), vraw);
+            for (int q4 = 0; q4 < 4; ++q4) {  // coefficients 4 q4 .. 4 q4 + 3, vector loads
+                float h0[4], h1[4], h2[4], hv[4];
+                load_sh_run<ShT, 4>(hc, hw, 4 * q4, h0, h1, h2, hv);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int k = 4 * q4 + j;
+                    craw[0] = fmaf(Y[k], h0[j], craw[0]);
+                    craw[1] = fmaf(Y[k], h1[j], craw[1]);
+                    craw[2] = fmaf(Y[k], h2[j], craw[2]);
+                    vraw = fmaf(Y[k], hv[j], vraw);
+                }
             }
             // Eq. 1: w = max(0, 1 - z/sigma) max(0, vraw)
             const float zterm = 1.f - z / sp.sigma;
@@ -126,13 +132,18 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(const __grid_constant_
             const float m0 = craw[0] > 0.f ? gc[0] : 0.f, m1 = craw[1] > 0.f ? gc[1] : 0.f,
                         m2 = craw[2] > 0.f ? gc[2] : 0.f, mv = vraw > 0.f ? gv : 0.f;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                g_h[3 * k + 0] = fmaf(m0, Y[k], g_h[3 * k + 0]);
-                g_h[3 * k + 1] = fmaf(m1, Y[k], g_h[3 * k + 1]);
-                g_h[3 * k + 2] = fmaf(m2, Y[k], g_h[3 * k + 2]);
-                g_hw[k] = fmaf(mv, Y[k], g_hw[k]);
-                coef[k] = m0 * ldf(hc, 3 * k + 0) + m1 * ldf(hc, 3 * k + 1) + m2 * ldf(hc, 3 * k + 2) +
-                          mv * ldf(hw, k);
+            for (int q4 = 0; q4 < 4; ++q4) {
+                float h0[4], h1[4], h2[4], hv[4];
+                load_sh_run<ShT, 4>(hc, hw, 4 * q4, h0, h1, h2, hv);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int k = 4 * q4 + j;
+                    g_h[3 * k + 0] = fmaf(m0, Y[k], g_h[3 * k + 0]);
+                    g_h[3 * k + 1] = fmaf(m1, Y[k], g_h[3 * k + 1]);
+                    g_h[3 * k + 2] = fmaf(m2, Y[k], g_h[3 * k + 2]);
+                    g_hw[k] = fmaf(mv, Y[k], g_hw[k]);
+                    coef[k] = m0 * h0[j] + m1 * h1[j] + m2 * h2[j] + mv * hv[j];
+                }
             }
             float gdir[3];
             sh_grad16(nx, ny, nz, coef, gdir);
