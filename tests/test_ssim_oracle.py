@@ -58,3 +58,25 @@ def test_pure_ssim_term_gradient_and_lambda():
     xm[4, 5, 1] -= h
     fd = ((1 - osm.ssim(xp, y)) - (1 - osm.ssim(xm, y))) / (2 * h)
     assert abs(fd - g1[4, 5, 1]) < 1e-8
+
+
+def test_closed_form_on_a_checkerboard_against_a_constant():
+    # x = a + d (-1)^(i+j), y = b: at an interior pixel mu_x = a + d s c^2 (s = (-1)^(i+j),
+    # c = sum_k w_k (-1)^(k-5)), E[x^2] = a^2 + 2 a d s c^2 + d^2, so s_xx = d^2 (1 - c^4);
+    # mu_y = b, s_yy = 0, s_xy = 0: S = (2 mu_x b + C1) C2 / ((mu_x^2 + b^2 + C1)(s_xx + C2))
+    a, d, b = 0.4, 0.1, 0.7
+    n = 31
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    x = a + d * (-1.0) ** (i + j)
+    y = np.full((n, n), b)
+    S, _, _, _ = osm.ssim_maps(x, y)
+    w = osm.window_1d()
+    c = np.sum(w * (-1.0) ** (np.arange(11) - 5))
+    for (p, q) in [(15, 15), (12, 17), (8, 9)]:
+        s = (-1.0) ** (p + q)
+        mx = a + d * s * c * c
+        sxx = d * d * (1 - c ** 4)
+        want = (2 * mx * b + osm.C1) * osm.C2 / ((mx * mx + b * b + osm.C1) * (sxx + osm.C2))
+        assert abs(S[p, q] - want) < 1e-12, (p, q, S[p, q], want)
+    # the constants are those of 3DGS (data range 1)
+    assert osm.C1 == 0.01 ** 2 and osm.C2 == 0.03 ** 2 and osm.LAMBDA == 0.2
