@@ -985,8 +985,41 @@ def main():
             stream.synchronize()
             prof_rows = r.get_profile()
             r.set_profiling(False)
+        # end to end on the stage layout: each step copies the active rows (not the whole scene) and
+        # the target from pinned host memory and reads back the compact gradients and the loss
+        host_a = {k: getattr(spa, k).cpu().pin_memory() for k in PARAM_NAMES}
+        host_target = target.cpu().pin_memory()
+        host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
+        host_loss = torch.empty(1).pin_memory()
+        h2d_a = sum(v.numel() * v.element_size() for v in host_a.values()) + host_target.numel() * 4
+        d2h_a = sum(v.numel() * v.element_size() for v in out.values()) + 4
+
+        def e2e_rows_step():
+            for k, v in host_a.items():
+                getattr(spa, k).copy_(v, non_blocking=True)
+            target.copy_(host_target, non_blocking=True)
+            step_active_rows()
+            for k, v in out.items():
+                host_out[k].copy_(v, non_blocking=True)
+            host_loss.copy_(loss, non_blocking=True)
+
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                e2e_rows_step()
+            stream.synchronize()
+            e_t = []
+            for _ in range(args.steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                e2e_rows_step()
+                b.record(stream)
+                stream.synchronize()
+                e_t.append(a.elapsed_time(b))
         active_rows = {"gather_ms_per_stage": gather_ms, "step_ms": step_rows_ms, "train_iteration_ms": train_rows_ms,
-                       "per_kernel_ms": {k: v[1] / max(1, v[0]) for k, v in prof_rows.items()}}
+                       "per_kernel_ms": {k: v[1] / max(1, v[0]) for k, v in prof_rows.items()},
+                       "e2e": {"ms_per_step": float(np.mean(e_t)), "value": head["E"] / (float(np.mean(e_t)) * 1e-3),
+                               "unit": UNIT, "h2d_bytes_per_step": int(h2d_a), "d2h_bytes_per_step": int(d2h_a)}}
         train = {"ms": train_ms, "adam_ms": adam_ms, "adam_gbs": adam_bytes / (adam_ms * 1e-3) / 1e9,
                  "adam_hbm_frac": adam_bytes / (adam_ms * 1e-3) / 1e9 / float(_peaks()[0].get("hbm_gbs", 6800.0)),
                  "adam_algorithmic_bytes": adam_bytes, "active_rows_layout": active_rows}

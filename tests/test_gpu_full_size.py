@@ -125,3 +125,31 @@ def test_batched_3m_four_resolutions_windows():
                 total[k] = total[k] + rg[k]
             total["amb"] = total["amb"] | rg["amb"]
     check_against_oracle(grads, total, np.where(act)[0])
+
+
+def test_unbounded_1m_dssim_loss_at_full_view():
+    """The 3DGS loss (0.8 L1 + 0.2 D-SSIM) of the 1297x840 view at 1M splats / 5 %: the loss and
+    dL/dC against the FP64 oracle's SSIM on the same (library-rendered) image."""
+    from oracle import ssim as osm
+    c = scenes.UNBOUNDED
+    scene, cam, target_np = scenes.unbounded_workload()
+    n, W, H = c["n"], c["width"], c["height"]
+    mask_np = scenes.unbounded_active_mask(scene, 0.05)
+    sp = SplatParams.from_numpy(scene)
+    r = Renderer(n, [(W, H)], max_pairs=1 << 27)
+    r.set_active(torch.as_tensor(mask_np, device="cuda"))
+    r.commit_frozen(sp, cam, 0, mode="recompute")
+    (img,), _ = r.forward(sp, [cam], [0])
+    x = to_np(img)
+    t = target_np.astype(np.float64)
+    d = x - t
+    t = np.where((np.abs(d) < 1e-6) & (d != 0), t - 1e-6 * np.sign(d), t).astype(np.float32)  # no L1 sign ties
+    gimg = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
+    loss = r.loss_l1_dssim([torch.as_tensor(t, device="cuda")], 0.2, grad_images=[gimg])
+    r.backward(sp)
+    r.status()
+    lref = osm.loss_l1_dssim(x, t, 0.2)
+    assert abs(loss.item() - lref) <= 1e-5 * abs(lref), (loss.item(), lref)
+    gref = osm.grad_l1_dssim(x, t, 0.2)
+    err = np.abs(to_np(gimg) - gref).max() / np.abs(gref).max()
+    assert err <= 1e-4, err
