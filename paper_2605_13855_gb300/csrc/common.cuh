@@ -31,6 +31,12 @@ constexpr int kMaxViews = 32;
 constexpr float kNearZ = 0.2f;                  // near-plane cull (3DGS convention)
 constexpr float kDilation = 0.3f;               // low-pass dilation of Sigma' (3DGS convention)
 constexpr float kAlphaMax = 0.99f;              // opacity clamp (3DGS convention)
+// About log2(0.989): a splat with log2 o at or below it never reaches the clamp.
+// Its raw alpha is 2^(log2 o - s) with s >= 0, at most 2^-0.015957 = 0.98900
+// before the approximate exp2 errs by a few ulp (1e-5 relative would still
+// stay below 0.99), so the rasters skip min(., 0.99) for it with identical
+// results.
+constexpr float kNoClampLog2 = -0.015957f;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 constexpr float kLog2_255 = 7.9943534368588578f;  // log2(255); alpha_raw >= 1/255 <=> log2 alpha_raw >= -this

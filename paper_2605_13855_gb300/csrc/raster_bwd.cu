@@ -39,10 +39,11 @@ namespace soit {
 //
 // Each lane evaluates two adjacent columns per step with paired FP32
 // instructions (f32x2 FMA / multiply / add, one issue slot for two values);
-// the pixel states sit in shared memory as planes so that one 64-bit load
-// fetches a component for both pixels.  Components of the paired operations
-// round exactly like their scalar counterparts, so contribution decisions
-// stay identical to the forward raster's.
+// the pixel states sit in shared memory with the components of two adjacent
+// pixels side by side, so that three broadcast loads fetch a pixel pair.
+// Components of the paired operations round exactly like their scalar
+// counterparts, so contribution decisions stay identical to the forward
+// raster's.
 constexpr int kBwdKeys = 18;  // splat classes of the optional per-round ordering
 
 // Per-lane accumulators of one splat over the tile (see the sums above).
@@ -55,13 +56,23 @@ struct BwdSplat {
     float A2dx0, dy0, rA2, B2, thr;
 };
 
+// Pixel state of the tile, two adjacent pixels per component: sA = (B g0, B g1),
+// sB = (B g2, A), sC = -B g.F, so that one pixel pair costs three broadcast loads.
+struct BwdState {
+    float4 sA[kTilePix / 2], sB[kTilePix / 2];
+    float2 sC[kTilePix / 2];
+};
+
 // Rows [rlo, rhi] of the tile for one lane's splat, two adjacent pixels per
 // step.  kTest: test every pixel against the cutoff (the pair contributes iff
 // s <= thr); without it every pixel of the rows contributes (the caller knows
-// the whole tile lies inside the cutoff ellipse).
-template <bool kTest>
-__device__ __forceinline__ void bwd_rows(const BwdSplat &bs, const float2 (*sp)[kTilePix / 2], int rlo, int rhi,
-                                         BwdAcc &acc) {
+// the whole tile lies inside the cutoff ellipse).  The body of a step runs
+// when some lane of the warp has a contributing pixel (a warp vote, so the
+// branch is uniform); lanes without one run it with a = 0, which adds exact
+// zeros.  kClamp: some lane's splat can reach the 0.99 clamp; without it
+// min(a, 0.99) = a and the clamp selects are left out (same results).
+template <bool kTest, bool kClamp>
+__device__ __forceinline__ void bwd_rows(const BwdSplat &bs, const BwdState &S, int rlo, int rhi, BwdAcc &acc) {
     const float2 zero2 = make_float2(0.f, 0.f);
     const float2 m1 = make_float2(-1.f, -1.f), one2 = make_float2(1.f, 1.f);
     for (int ky = rlo; ky <= rhi; ++ky) {
@@ -73,16 +84,24 @@ __device__ __forceinline__ void bwd_rows(const BwdSplat &bs, const float2 (*sp)[
             const float2 e1 = __ffma2_rn(bs.A2p, make_float2((float)(2 * kp), (float)(2 * kp + 1)), e10p);
             const float2 sq = __ffma2_rn(e1, e1, e2p);
             const bool in0 = !kTest || sq.x <= bs.thr, in1 = !kTest || sq.y <= bs.thr;
-            if (in0 || in1) {
+            if (!kTest || __any_sync(0xffffffffu, in0 || in1)) {
                 const int kk = ky * (kTile / 2) + kp;
-                const float2 b0 = sp[0][kk], b1 = sp[1][kk], b2 = sp[2][kk];
-                const float2 Ap = sp[3][kk], nbF = sp[4][kk];
+                const float4 ua = S.sA[kk], ub = S.sB[kk];
+                const float2 nbF = S.sC[kk];
+                const float2 b0 = make_float2(ua.x, ua.y), b1 = make_float2(ua.z, ua.w);
+                const float2 b2 = make_float2(ub.x, ub.y), Ap = make_float2(ub.z, ub.w);
                 // log2 o - s: -s + log2 o rounds once, exactly like the forward's subtraction
                 const float2 lg = __ffma2_rn(sq, m1, bs.l2op);
                 const float ar0 = fast_exp2(lg.x), ar1 = fast_exp2(lg.y);
-                const float2 a = make_float2(in0 ? fminf(ar0, kAlphaMax) : 0.f, in1 ? fminf(ar1, kAlphaMax) : 0.f);
-                // the alpha path (o, mu', conic) is off where alpha is clamped
-                const float2 am = make_float2(ar0 > kAlphaMax ? 0.f : a.x, ar1 > kAlphaMax ? 0.f : a.y);
+                float2 a, am;
+                if (kClamp) {
+                    a = make_float2(in0 ? fminf(ar0, kAlphaMax) : 0.f, in1 ? fminf(ar1, kAlphaMax) : 0.f);
+                    // the alpha path (o, mu', conic) is off where alpha is clamped
+                    am = make_float2(ar0 > kAlphaMax ? 0.f : a.x, ar1 > kAlphaMax ? 0.f : a.y);
+                } else {
+                    a = make_float2(in0 ? ar0 : 0.f, in1 ? ar1 : 0.f);
+                    am = a;
+                }
                 const float2 D = __ffma2_rn(b0, bs.c0p, __ffma2_rn(b1, bs.c1p, __ffma2_rn(b2, bs.c2p, nbF)));
                 const float2 oma = __ffma2_rn(a, m1, one2);  // 1 - a
                 const float2 inv = make_float2(fast_rcp(oma.x), fast_rcp(oma.y));
@@ -113,8 +132,7 @@ __global__ void __launch_bounds__(kTilePix, 4) raster_bwd_kernel(const __grid_co
                                                               const int *__restrict__ offsets,
                                                               const uint32_t *__restrict__ pairs, int64_t cap,
                                                               uint32_t nrec, float4 *__restrict__ sgrad) {
-    // pixel state planes, two adjacent pixels per float2: B g0, B g1, B g2, A, -B g.F
-    __shared__ float2 sp[5][kTilePix / 2];
+    __shared__ BwdState S;
     __shared__ uint32_t sorted[kGroup ? kTilePix : 1];
     __shared__ uint8_t sfull[kGroup ? kTilePix : 1];
     __shared__ int hist[kBwdKeys];
@@ -134,8 +152,13 @@ __global__ void __launch_bounds__(kTilePix, 4) raster_bwd_kernel(const __grid_co
 #pragma unroll
             for (int k = 0; k < 5; ++k) st5[k] = st[k * HW + pix];
         }
-#pragma unroll
-        for (int k = 0; k < 5; ++k) reinterpret_cast<float *>(sp[k])[tid] = st5[k];
+        // pixel tid is component (tid & 1) of pixel pair tid >> 1
+        const int kk = tid >> 1, c = tid & 1;
+        reinterpret_cast<float *>(S.sA)[4 * kk + c] = st5[0];
+        reinterpret_cast<float *>(S.sA)[4 * kk + 2 + c] = st5[1];
+        reinterpret_cast<float *>(S.sB)[4 * kk + c] = st5[2];
+        reinterpret_cast<float *>(S.sB)[4 * kk + 2 + c] = st5[3];
+        reinterpret_cast<float *>(S.sC)[tid] = st5[4];
     }
     __syncthreads();
 
@@ -227,10 +250,18 @@ __global__ void __launch_bounds__(kTilePix, 4) raster_bwd_kernel(const __grid_co
         acc.See = acc.gw = acc.gc0 = acc.gc1 = acc.gc2 = zero2;
         acc.Se = acc.Sey = acc.Sd = acc.Sdy = acc.Sdyy = 0.f;
         const BwdSplat bs{A2p, wp, l2op, c0p, c1p, c2p, sc.A2dx0, dy0, sc.rA2, B2, sc.thr};
-        if (kGroup && __all_sync(0xffffffffu, full || !valid))
-            bwd_rows<false>(bs, sp, 0, kTile - 1, acc);  // every pixel of the tile contributes
-        else
-            bwd_rows<true>(bs, sp, rlo, rhi, acc);
+        // a splat with log2 o <= kNoClampLog2 never reaches the 0.99 clamp
+        const bool clamp = __any_sync(0xffffffffu, valid && log2o > kNoClampLog2);
+        if (kGroup && __all_sync(0xffffffffu, full || !valid)) {  // every pixel of the tile contributes
+            if (clamp)
+                bwd_rows<false, true>(bs, S, 0, kTile - 1, acc);
+            else
+                bwd_rows<false, false>(bs, S, 0, kTile - 1, acc);
+        } else if (clamp) {
+            bwd_rows<true, true>(bs, S, rlo, rhi, acc);
+        } else {
+            bwd_rows<true, false>(bs, S, rlo, rhi, acc);
+        }
         const float Se = acc.Se, Sey = acc.Sey, Sd = acc.Sd, Sdy = acc.Sdy, Sdyy = acc.Sdyy;
         const float2 See = acc.See, gw = acc.gw, gc0 = acc.gc0, gc1 = acc.gc1, gc2 = acc.gc2;
         if (valid) {

@@ -49,6 +49,77 @@ __device__ __forceinline__ void strip_exponents(float A2, float e10, float e2sq,
     }
 }
 
+// One staged batch of n records into the thread's strip: two-level summation,
+// 32-splat blocks added to the totals.  kClamp: some record of the batch can
+// reach the 0.99 clamp; without it min(a, 0.99) = a and the min is left out.
+template <int kMode, bool kCount, int kStrip, bool kClamp>
+__device__ __forceinline__ void fwd_batch(const float4 *s0, const float4 *s1, const float4 *s2, const float *ssign,
+                                          const uint8_t *sfl, int n, int ky, int sx, int wrow, int tx, int ty,
+                                          const ViewDesc &vd, float2 *P01, float2 *P2Q, float *T,
+                                          unsigned &n_contrib) {
+    constexpr int kStripsPerRow = kTile / kStrip;
+    for (int jb = 0; jb < n; jb += 32) {
+        float2 b01[kStrip], b2q[kStrip];
+        float bl[kStrip];
+#pragma unroll
+        for (int j = 0; j < kStrip; ++j) {
+            b01[j] = b2q[j] = make_float2(0.f, 0.f);
+            bl[j] = 0.f;
+        }
+        const int je = min(n, jb + 32);
+        for (int j = jb; j < je; ++j) {
+            const float4 a0 = s0[j], a1 = s1[j];
+            if (sfl[j]) {  // block-uniform: every pixel of the tile contributes, no cutoff test
+                const RowTerms rt = row_terms(a0.x, a0.y, a0.z, a1.x, ky);
+                const float4 a2 = s2[j];
+                float sq[kStrip], lg[kStrip];
+                strip_exponents<kStrip>(a0.w, rt.e10, rt.e2sq, a1.z, sx, sq, lg);
+#pragma unroll
+                for (int p = 0; p < kStrip; ++p) {
+                    const float a = kClamp ? fminf(fast_exp2(lg[p]), kAlphaMax) : fast_exp2(lg[p]);
+                    const float2 aa = make_float2(a, a);
+                    b01[p] = __ffma2_rn(aa, make_float2(a2.x, a2.y), b01[p]);
+                    b2q[p] = __ffma2_rn(aa, make_float2(a2.z, a2.w), b2q[p]);
+                    if (kMode == kRasterSums)
+                        bl[p] = fmaf(ssign[j], log1pf(-a), bl[p]);
+                    else
+                        T[p] = fmaf(-T[p], a, T[p]);
+                    if (kCount) n_contrib += (tx * kTile + sx + p < vd.W && ty * kTile + ky < vd.H) ? 1u : 0u;
+                }
+                continue;
+            }
+            // warp-uniform: the ellipse misses this warp's rows
+            const float dlo = a0.y + (float)wrow;
+            if (dlo > a1.w || dlo + (float)(32 / kStripsPerRow - 1) < -a1.w) continue;
+            const RowTerms rt = row_terms(a0.x, a0.y, a0.z, a1.x, ky);
+            if (rt.e2sq > a1.y) continue;  // whole row outside (s >= e2^2 for every pixel of it)
+            const float4 a2 = s2[j];
+            float sq[kStrip], lg[kStrip];
+            strip_exponents<kStrip>(a0.w, rt.e10, rt.e2sq, a1.z, sx, sq, lg);
+#pragma unroll
+            for (int p = 0; p < kStrip; ++p) {
+                if (sq[p] <= a1.y) {
+                    const float a = kClamp ? fminf(fast_exp2(lg[p]), kAlphaMax) : fast_exp2(lg[p]);
+                    const float2 aa = make_float2(a, a);
+                    b01[p] = __ffma2_rn(aa, make_float2(a2.x, a2.y), b01[p]);
+                    b2q[p] = __ffma2_rn(aa, make_float2(a2.z, a2.w), b2q[p]);
+                    if (kMode == kRasterSums)
+                        bl[p] = fmaf(ssign[j], log1pf(-a), bl[p]);
+                    else
+                        T[p] = fmaf(-T[p], a, T[p]);
+                    if (kCount) n_contrib += (tx * kTile + sx + p < vd.W && ty * kTile + ky < vd.H) ? 1u : 0u;
+                }
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < kStrip; ++p) {
+            P01[p] = __fadd2_rn(P01[p], b01[p]);
+            P2Q[p] = __fadd2_rn(P2Q[p], b2q[p]);
+            if (kMode == kRasterSums) T[p] += bl[p];
+        }
+    }
+}
+
 template <int kMode, bool kCount, int kStrip>
 __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip == 2 ? 4 : 8)) raster_fwd_kernel(const __grid_constant__ Batch b,
                                                                  const float4 *__restrict__ rec,
@@ -91,6 +162,7 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
     for (int base = start; base < end; base += kFwdBatch) {
         const int n = min(kFwdBatch, end - base);
         __syncthreads();
+        int may_clamp = 0;  // some staged splat can reach the 0.99 clamp
         for (int k = tid; k < n; k += kFwdThreads) {
             const uint32_t q = pairs[base + k];
             // staged: s0 = (A2 dx0, dy0, r A2, A2), s1 = (B2, thr, log2 o, yh),
@@ -117,6 +189,7 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
                         in = in && quad_s(col_e1(a0.w, rt.e10, cxx * (kTile - 1)), rt.e2sq) <= lim;
                 }
                 full = in;
+                may_clamp |= a1.y > kNoClampLog2 ? 1 : 0;
                 const float ws = kMode == kRasterSums ? a1.z * a2.w : a1.z;
                 t2 = make_float4(ws * a2.x, ws * a2.y, ws * a2.z, ws);
             }
@@ -126,68 +199,12 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
             sfl[k] = full ? 1 : 0;
             if (kMode == kRasterSums) ssign[k] = q < nrec ? rec[3 * (int64_t)q + 2].w : 0.f;
         }
-        __syncthreads();
-        // two-level summation: 32-splat blocks into the total
-        for (int jb = 0; jb < n; jb += 32) {
-        float2 b01[kStrip], b2q[kStrip];
-        float bl[kStrip];
-#pragma unroll
-        for (int j = 0; j < kStrip; ++j) {
-            b01[j] = b2q[j] = make_float2(0.f, 0.f);
-            bl[j] = 0.f;
-        }
-        const int je = min(n, jb + 32);
-        for (int j = jb; j < je; ++j) {
-            const float4 a0 = s0[j], a1 = s1[j];
-            if (sfl[j]) {  // block-uniform: every pixel of the tile contributes, no cutoff test
-                const RowTerms rt = row_terms(a0.x, a0.y, a0.z, a1.x, ky);
-                const float4 a2 = s2[j];
-                float sq[kStrip], lg[kStrip];
-                strip_exponents<kStrip>(a0.w, rt.e10, rt.e2sq, a1.z, sx, sq, lg);
-#pragma unroll
-                for (int p = 0; p < kStrip; ++p) {
-                    const float a = fminf(fast_exp2(lg[p]), kAlphaMax);
-                    const float2 aa = make_float2(a, a);
-                    b01[p] = __ffma2_rn(aa, make_float2(a2.x, a2.y), b01[p]);
-                    b2q[p] = __ffma2_rn(aa, make_float2(a2.z, a2.w), b2q[p]);
-                    if (kMode == kRasterSums)
-                        bl[p] = fmaf(ssign[j], log1pf(-a), bl[p]);
-                    else
-                        T[p] = fmaf(-T[p], a, T[p]);
-                    if (kCount) n_contrib += (tx * kTile + sx + p < vd.W && ty * kTile + ky < vd.H) ? 1u : 0u;
-                }
-                continue;
-            }
-            // warp-uniform: the ellipse misses this warp's rows
-            const float dlo = a0.y + (float)wrow;
-            if (dlo > a1.w || dlo + (float)(32 / kStripsPerRow - 1) < -a1.w) continue;
-            const RowTerms rt = row_terms(a0.x, a0.y, a0.z, a1.x, ky);
-            if (rt.e2sq > a1.y) continue;  // whole row outside (s >= e2^2 for every pixel of it)
-            const float4 a2 = s2[j];
-            float sq[kStrip], lg[kStrip];
-            strip_exponents<kStrip>(a0.w, rt.e10, rt.e2sq, a1.z, sx, sq, lg);
-#pragma unroll
-            for (int p = 0; p < kStrip; ++p) {
-                if (sq[p] <= a1.y) {
-                    const float a = fminf(fast_exp2(lg[p]), kAlphaMax);
-                    const float2 aa = make_float2(a, a);
-                    b01[p] = __ffma2_rn(aa, make_float2(a2.x, a2.y), b01[p]);
-                    b2q[p] = __ffma2_rn(aa, make_float2(a2.z, a2.w), b2q[p]);
-                    if (kMode == kRasterSums)
-                        bl[p] = fmaf(ssign[j], log1pf(-a), bl[p]);
-                    else
-                        T[p] = fmaf(-T[p], a, T[p]);
-                    if (kCount) n_contrib += (tx * kTile + sx + p < vd.W && ty * kTile + ky < vd.H) ? 1u : 0u;
-                }
-            }
-        }
-#pragma unroll
-        for (int p = 0; p < kStrip; ++p) {
-            P01[p] = __fadd2_rn(P01[p], b01[p]);
-            P2Q[p] = __fadd2_rn(P2Q[p], b2q[p]);
-            if (kMode == kRasterSums) T[p] += bl[p];
-        }
-        }
+        if (__syncthreads_or(may_clamp))
+            fwd_batch<kMode, kCount, kStrip, true>(s0, s1, s2, ssign, sfl, n, ky, sx, wrow, tx, ty, vd, P01, P2Q, T,
+                                                   n_contrib);
+        else
+            fwd_batch<kMode, kCount, kStrip, false>(s0, s1, s2, ssign, sfl, n, ky, sx, wrow, tx, ty, vd, P01, P2Q, T,
+                                                    n_contrib);
     }
 
     const int64_t HW = (int64_t)vd.W * vd.H;

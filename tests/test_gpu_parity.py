@@ -168,6 +168,28 @@ def test_ragged_views_and_culled_splats():
         _check_view(r, sp, scene, c, v, mask, seed=10 + v)
 
 
+def test_high_opacity_clamped_pairs():
+    """Splats opaque enough that alpha reaches the 0.99 clamp near their
+    centres (opacity up to 0.9997), a few among ordinary ones: tiles and warps
+    with and without such splats take the rasters' clamping and clamp-free
+    paths, both against the oracle."""
+    rng = np.random.default_rng(5)
+    n = 3000
+    scene = scenes.uniform_cube_scene(n, 91)
+    hi = rng.choice(n, 60, replace=False)
+    scene["opacity_logits"][hi] = rng.uniform(4.0, 8.0, size=hi.size)
+    scene["log_scales"][hi] += 2.5  # wide enough that several pixels lie where alpha exceeds 0.99
+    cams = [scenes.random_camera(92, 96, 80), scenes.random_camera(93, 53, 37)]
+    mask = (rng.uniform(size=n) < 0.7).astype(np.uint8)
+    r, sp = _renderer_for(scene, cams, mask)
+    clamped = 0
+    for v, c in enumerate(cams):
+        _check_view(r, sp, scene, c, v, mask, seed=30 + v)
+        _, _, stats = oracle.render_sums(scene, c)
+        clamped += int(stats[1])
+    assert clamped > 0  # some pairs were clamped at 0.99
+
+
 def test_multiview_batch_equals_single_views():
     n = 8000
     scene = scenes.unbounded_scene(n, 3100)
