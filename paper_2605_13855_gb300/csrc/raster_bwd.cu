@@ -39,8 +39,8 @@ namespace soit {
 //
 // Each lane evaluates two adjacent columns per step with paired FP32
 // instructions (f32x2 FMA / multiply / add, one issue slot for two values);
-// the pixel states sit in shared memory with the components of two adjacent
-// pixels side by side, so that three broadcast loads fetch a pixel pair.
+// the pixel states sit in shared memory as planes, so that one 128-bit
+// broadcast load fetches a component for two steps.
 // Components of the paired operations round exactly like their scalar
 // counterparts, so contribution decisions stay identical to the forward
 // raster's.
@@ -56,65 +56,91 @@ struct BwdSplat {
     float A2dx0, dy0, rA2, B2, thr;
 };
 
-// Pixel state of the tile, two adjacent pixels per component: sA = (B g0, B g1),
-// sB = (B g2, A), sC = -B g.F, so that one pixel pair costs three broadcast loads.
+// Pixel state of the tile: five planes (B g0, B g1, B g2, A, -B g.F), four
+// adjacent pixels of a row per float4, so that five broadcast loads fetch
+// the state of two steps.
 struct BwdState {
-    float4 sA[kTilePix / 2], sB[kTilePix / 2];
-    float2 sC[kTilePix / 2];
+    float4 p[5][kTilePix / 4];
 };
 
-// Rows [rlo, rhi] of the tile for one lane's splat, two adjacent pixels per
-// step.  kTest: test every pixel against the cutoff (the pair contributes iff
-// s <= thr); without it every pixel of the rows contributes (the caller knows
-// the whole tile lies inside the cutoff ellipse).  The body of a step runs
-// when some lane of the warp has a contributing pixel (a warp vote, so the
-// branch is uniform); lanes without one run it with a = 0, which adds exact
-// zeros.  kClamp: some lane's splat can reach the 0.99 clamp; without it
-// min(a, 0.99) = a and the clamp selects are left out (same results).
-template <bool kTest, bool kClamp>
+// One step of a lane: pixels (2k, 2k + 1) of a row against the lane's splat,
+// given their exponents and cutoff decisions; lanes without a contributing
+// pixel run it with a = 0, which adds exact zeros.  kClamp: some lane's splat
+// can reach the 0.99 clamp; without it min(a, 0.99) = a and the clamp
+// selects are left out (same results).
+template <bool kClamp>
+__device__ __forceinline__ void bwd_step(const BwdSplat &bs, float2 e1, float2 sq, bool in0, bool in1, float2 b0,
+                                         float2 b1, float2 b2, float2 Ap, float2 nbF, float2 &Rd, float2 &Re,
+                                         BwdAcc &acc) {
+    const float2 m1 = make_float2(-1.f, -1.f), one2 = make_float2(1.f, 1.f);
+    // log2 o - s: -s + log2 o rounds once, exactly like the forward's subtraction
+    const float2 lg = __ffma2_rn(sq, m1, bs.l2op);
+    const float ar0 = fast_exp2(lg.x), ar1 = fast_exp2(lg.y);
+    float2 a, am;
+    if (kClamp) {
+        a = make_float2(in0 ? fminf(ar0, kAlphaMax) : 0.f, in1 ? fminf(ar1, kAlphaMax) : 0.f);
+        // the alpha path (o, mu', conic) is off where alpha is clamped
+        am = make_float2(ar0 > kAlphaMax ? 0.f : a.x, ar1 > kAlphaMax ? 0.f : a.y);
+    } else {
+        a = make_float2(in0 ? ar0 : 0.f, in1 ? ar1 : 0.f);
+        am = a;
+    }
+    const float2 D = __ffma2_rn(b0, bs.c0p, __ffma2_rn(b1, bs.c1p, __ffma2_rn(b2, bs.c2p, nbF)));
+    const float2 oma = __ffma2_rn(a, m1, one2);  // 1 - a
+    const float2 inv = make_float2(fast_rcp(oma.x), fast_rcp(oma.y));
+    const float2 dLda = __ffma2_rn(Ap, inv, __fmul2_rn(bs.wp, D));
+    acc.gw = __ffma2_rn(a, D, acc.gw);
+    acc.gc0 = __ffma2_rn(a, b0, acc.gc0);  // times w in the epilogue
+    acc.gc1 = __ffma2_rn(a, b1, acc.gc1);
+    acc.gc2 = __ffma2_rn(a, b2, acc.gc2);
+    const float2 da = __fmul2_rn(dLda, am);
+    Rd = __fadd2_rn(Rd, da);
+    const float2 qd = __fmul2_rn(da, e1);
+    Re = __fadd2_rn(Re, qd);
+    acc.See = __ffma2_rn(qd, e1, acc.See);
+}
+
+// Rows [rlo, rhi] of the tile for one lane's splat.  kTest: test every pixel
+// against the cutoff (the pair contributes iff s <= thr); without it every
+// pixel of the rows contributes (the caller knows the whole tile lies inside
+// the cutoff ellipse).  A row is taken kQuads groups of four pixels at a
+// time: the group's two or four steps run when some lane of the warp has a
+// contributing pixel in it (a warp vote, so the branch is uniform), and run
+// without branches between them, so that their chains interleave.
+template <bool kTest, bool kClamp, int kQuads>
 __device__ __forceinline__ void bwd_rows(const BwdSplat &bs, const BwdState &S, int rlo, int rhi, BwdAcc &acc) {
     const float2 zero2 = make_float2(0.f, 0.f);
-    const float2 m1 = make_float2(-1.f, -1.f), one2 = make_float2(1.f, 1.f);
     for (int ky = rlo; ky <= rhi; ++ky) {
         const RowTerms rt = row_terms(bs.A2dx0, bs.dy0, bs.rA2, bs.B2, ky);
         const float2 e10p = make_float2(rt.e10, rt.e10), e2p = make_float2(rt.e2sq, rt.e2sq);
         float2 Rd = zero2, Re = zero2;
 #pragma unroll
-        for (int kp = 0; kp < kTile / 2; ++kp) {
-            const float2 e1 = __ffma2_rn(bs.A2p, make_float2((float)(2 * kp), (float)(2 * kp + 1)), e10p);
-            const float2 sq = __ffma2_rn(e1, e1, e2p);
-            const bool in0 = !kTest || sq.x <= bs.thr, in1 = !kTest || sq.y <= bs.thr;
-            if (!kTest || __any_sync(0xffffffffu, in0 || in1)) {
-                const int kk = ky * (kTile / 2) + kp;
-                const float4 ua = S.sA[kk], ub = S.sB[kk];
-                const float2 nbF = S.sC[kk];
-                const float2 b0 = make_float2(ua.x, ua.y), b1 = make_float2(ua.z, ua.w);
-                const float2 b2 = make_float2(ub.x, ub.y), Ap = make_float2(ub.z, ub.w);
-                // log2 o - s: -s + log2 o rounds once, exactly like the forward's subtraction
-                const float2 lg = __ffma2_rn(sq, m1, bs.l2op);
-                const float ar0 = fast_exp2(lg.x), ar1 = fast_exp2(lg.y);
-                float2 a, am;
-                if (kClamp) {
-                    a = make_float2(in0 ? fminf(ar0, kAlphaMax) : 0.f, in1 ? fminf(ar1, kAlphaMax) : 0.f);
-                    // the alpha path (o, mu', conic) is off where alpha is clamped
-                    am = make_float2(ar0 > kAlphaMax ? 0.f : a.x, ar1 > kAlphaMax ? 0.f : a.y);
-                } else {
-                    a = make_float2(in0 ? ar0 : 0.f, in1 ? ar1 : 0.f);
-                    am = a;
+        for (int kq0 = 0; kq0 < kTile / 4; kq0 += kQuads) {
+            float2 e1[2 * kQuads], sq[2 * kQuads];
+            bool in[4 * kQuads];
+            bool any = false;
+#pragma unroll
+            for (int h = 0; h < 2 * kQuads; ++h) {
+                const float kx = (float)(4 * kq0 + 2 * h);
+                e1[h] = __ffma2_rn(bs.A2p, make_float2(kx, kx + 1.f), e10p);
+                sq[h] = __ffma2_rn(e1[h], e1[h], e2p);
+                in[2 * h] = !kTest || sq[h].x <= bs.thr;
+                in[2 * h + 1] = !kTest || sq[h].y <= bs.thr;
+                any = any || in[2 * h] || in[2 * h + 1];
+            }
+            if (!kTest || __any_sync(0xffffffffu, any)) {
+#pragma unroll
+                for (int qq = 0; qq < kQuads; ++qq) {
+                    const int kq = ky * (kTile / 4) + kq0 + qq;
+                    const float4 u0 = S.p[0][kq], u1 = S.p[1][kq], u2 = S.p[2][kq], u3 = S.p[3][kq];
+                    const float4 u4 = S.p[4][kq];
+                    bwd_step<kClamp>(bs, e1[2 * qq], sq[2 * qq], in[4 * qq], in[4 * qq + 1], make_float2(u0.x, u0.y),
+                                     make_float2(u1.x, u1.y), make_float2(u2.x, u2.y), make_float2(u3.x, u3.y),
+                                     make_float2(u4.x, u4.y), Rd, Re, acc);
+                    bwd_step<kClamp>(bs, e1[2 * qq + 1], sq[2 * qq + 1], in[4 * qq + 2], in[4 * qq + 3],
+                                     make_float2(u0.z, u0.w), make_float2(u1.z, u1.w), make_float2(u2.z, u2.w),
+                                     make_float2(u3.z, u3.w), make_float2(u4.z, u4.w), Rd, Re, acc);
                 }
-                const float2 D = __ffma2_rn(b0, bs.c0p, __ffma2_rn(b1, bs.c1p, __ffma2_rn(b2, bs.c2p, nbF)));
-                const float2 oma = __ffma2_rn(a, m1, one2);  // 1 - a
-                const float2 inv = make_float2(fast_rcp(oma.x), fast_rcp(oma.y));
-                const float2 dLda = __ffma2_rn(Ap, inv, __fmul2_rn(bs.wp, D));
-                acc.gw = __ffma2_rn(a, D, acc.gw);
-                acc.gc0 = __ffma2_rn(a, b0, acc.gc0);  // times w in the epilogue
-                acc.gc1 = __ffma2_rn(a, b1, acc.gc1);
-                acc.gc2 = __ffma2_rn(a, b2, acc.gc2);
-                const float2 da = __fmul2_rn(dLda, am);
-                Rd = __fadd2_rn(Rd, da);
-                const float2 qd = __fmul2_rn(da, e1);
-                Re = __fadd2_rn(Re, qd);
-                acc.See = __ffma2_rn(qd, e1, acc.See);
             }
         }
         const float rd = Rd.x + Rd.y, re = Re.x + Re.y;
@@ -126,8 +152,10 @@ __device__ __forceinline__ void bwd_rows(const BwdSplat &bs, const BwdState &S, 
     }
 }
 
+constexpr int kBwdQuads = 2;  // groups of four pixels per warp vote
+
 template <bool kGroup>
-__global__ void __launch_bounds__(kTilePix, 4) raster_bwd_kernel(const __grid_constant__ Batch b,
+__global__ void __launch_bounds__(kTilePix, 3) raster_bwd_kernel(const __grid_constant__ Batch b,
                                                               const float4 *__restrict__ rec,
                                                               const int *__restrict__ offsets,
                                                               const uint32_t *__restrict__ pairs, int64_t cap,
@@ -152,13 +180,8 @@ __global__ void __launch_bounds__(kTilePix, 4) raster_bwd_kernel(const __grid_co
 #pragma unroll
             for (int k = 0; k < 5; ++k) st5[k] = st[k * HW + pix];
         }
-        // pixel tid is component (tid & 1) of pixel pair tid >> 1
-        const int kk = tid >> 1, c = tid & 1;
-        reinterpret_cast<float *>(S.sA)[4 * kk + c] = st5[0];
-        reinterpret_cast<float *>(S.sA)[4 * kk + 2 + c] = st5[1];
-        reinterpret_cast<float *>(S.sB)[4 * kk + c] = st5[2];
-        reinterpret_cast<float *>(S.sB)[4 * kk + 2 + c] = st5[3];
-        reinterpret_cast<float *>(S.sC)[tid] = st5[4];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) reinterpret_cast<float *>(S.p[k])[tid] = st5[k];
     }
     __syncthreads();
 
@@ -254,13 +277,13 @@ __global__ void __launch_bounds__(kTilePix, 4) raster_bwd_kernel(const __grid_co
         const bool clamp = __any_sync(0xffffffffu, valid && log2o > kNoClampLog2);
         if (kGroup && __all_sync(0xffffffffu, full || !valid)) {  // every pixel of the tile contributes
             if (clamp)
-                bwd_rows<false, true>(bs, S, 0, kTile - 1, acc);
+                bwd_rows<false, true, kBwdQuads>(bs, S, 0, kTile - 1, acc);
             else
-                bwd_rows<false, false>(bs, S, 0, kTile - 1, acc);
+                bwd_rows<false, false, kBwdQuads>(bs, S, 0, kTile - 1, acc);
         } else if (clamp) {
-            bwd_rows<true, true>(bs, S, rlo, rhi, acc);
+            bwd_rows<true, true, kBwdQuads>(bs, S, rlo, rhi, acc);
         } else {
-            bwd_rows<true, false>(bs, S, rlo, rhi, acc);
+            bwd_rows<true, false, kBwdQuads>(bs, S, rlo, rhi, acc);
         }
         const float Se = acc.Se, Sey = acc.Sey, Sd = acc.Sd, Sdy = acc.Sdy, Sdyy = acc.Sdyy;
         const float2 See = acc.See, gw = acc.gw, gc0 = acc.gc0, gc1 = acc.gc1, gc2 = acc.gc2;

@@ -49,67 +49,59 @@ __device__ __forceinline__ void strip_exponents(float A2, float e10, float e2sq,
     }
 }
 
-// One staged batch of n records into the thread's strip: two-level summation,
-// 32-splat blocks added to the totals.  kClamp: some record of the batch can
-// reach the 0.99 clamp; without it min(a, 0.99) = a and the min is left out.
-template <int kMode, bool kCount, int kStrip, bool kClamp>
-__device__ __forceinline__ void fwd_batch(const float4 *s0, const float4 *s1, const float4 *s2, const float *ssign,
-                                          const uint8_t *sfl, int n, int ky, int sx, int wrow, int tx, int ty,
-                                          const ViewDesc &vd, float2 *P01, float2 *P2Q, float *T,
-                                          unsigned &n_contrib) {
-    constexpr int kStripsPerRow = kTile / kStrip;
-    for (int jb = 0; jb < n; jb += 32) {
+// One staged record j against the thread's strip, accumulated into the
+// 32-splat block partials.  kTest: test every pixel against the cutoff
+// (without it the record's ellipse contains the whole tile).  The body has no
+// branches, so that the compiler can interleave two records.
+template <int kMode, bool kCount, int kStrip, bool kTest, bool kClamp>
+__device__ __forceinline__ void fwd_splat(const float4 *s0, const float4 *s1, const float4 *s2, const float *ssign,
+                                          int j, int ky, int sx, bool in_view_row, int x0, int W, float2 *b01,
+                                          float2 *b2q, float *bl, float *T, unsigned &n_contrib) {
+    const float4 a0 = s0[j], a1 = s1[j], a2 = s2[j];
+    const bool counted = kCount && j < kFwdBatch && in_view_row;  // the empty record counts nothing
+    const RowTerms rt = row_terms(a0.x, a0.y, a0.z, a1.x, ky);
+    float sq[kStrip], lg[kStrip];
+    strip_exponents<kStrip>(a0.w, rt.e10, rt.e2sq, a1.z, sx, sq, lg);
+#pragma unroll
+    for (int p = 0; p < kStrip; ++p) {
+        if (!kTest || sq[p] <= a1.y) {
+            const float ar = fast_exp2(lg[p]);
+            const float a = kClamp ? fminf(ar, kAlphaMax) : ar;
+            const float2 aa = make_float2(a, a);
+            b01[p] = __ffma2_rn(aa, make_float2(a2.x, a2.y), b01[p]);
+            b2q[p] = __ffma2_rn(aa, make_float2(a2.z, a2.w), b2q[p]);
+            if (kMode == kRasterSums)
+                bl[p] = fmaf(ssign[j], log1pf(-a), bl[p]);
+            else
+                T[p] = fmaf(-T[p], a, T[p]);
+            if (kCount) n_contrib += (counted && x0 + p < W) ? 1u : 0u;
+        }
+    }
+}
+
+// A list of staged records (indices into the staged arrays) into the
+// thread's strip, two records per iteration (the odd one out pairs with the
+// empty record at index kFwdBatch), summed in 32-record blocks that are added
+// to the totals (two-level summation).
+template <int kMode, bool kCount, int kStrip, bool kTest, bool kClamp>
+__device__ __forceinline__ void fwd_list(const float4 *s0, const float4 *s1, const float4 *s2, const float *ssign,
+                                         const uint16_t *list, int cnt, int ky, int sx, bool in_view_row, int x0,
+                                         int W, float2 *P01, float2 *P2Q, float *T, unsigned &n_contrib) {
+    for (int jb = 0; jb < cnt; jb += 32) {
         float2 b01[kStrip], b2q[kStrip];
         float bl[kStrip];
 #pragma unroll
-        for (int j = 0; j < kStrip; ++j) {
-            b01[j] = b2q[j] = make_float2(0.f, 0.f);
-            bl[j] = 0.f;
+        for (int p = 0; p < kStrip; ++p) {
+            b01[p] = b2q[p] = make_float2(0.f, 0.f);
+            bl[p] = 0.f;
         }
-        const int je = min(n, jb + 32);
-        for (int j = jb; j < je; ++j) {
-            const float4 a0 = s0[j], a1 = s1[j];
-            if (sfl[j]) {  // block-uniform: every pixel of the tile contributes, no cutoff test
-                const RowTerms rt = row_terms(a0.x, a0.y, a0.z, a1.x, ky);
-                const float4 a2 = s2[j];
-                float sq[kStrip], lg[kStrip];
-                strip_exponents<kStrip>(a0.w, rt.e10, rt.e2sq, a1.z, sx, sq, lg);
-#pragma unroll
-                for (int p = 0; p < kStrip; ++p) {
-                    const float a = kClamp ? fminf(fast_exp2(lg[p]), kAlphaMax) : fast_exp2(lg[p]);
-                    const float2 aa = make_float2(a, a);
-                    b01[p] = __ffma2_rn(aa, make_float2(a2.x, a2.y), b01[p]);
-                    b2q[p] = __ffma2_rn(aa, make_float2(a2.z, a2.w), b2q[p]);
-                    if (kMode == kRasterSums)
-                        bl[p] = fmaf(ssign[j], log1pf(-a), bl[p]);
-                    else
-                        T[p] = fmaf(-T[p], a, T[p]);
-                    if (kCount) n_contrib += (tx * kTile + sx + p < vd.W && ty * kTile + ky < vd.H) ? 1u : 0u;
-                }
-                continue;
-            }
-            // warp-uniform: the ellipse misses this warp's rows
-            const float dlo = a0.y + (float)wrow;
-            if (dlo > a1.w || dlo + (float)(32 / kStripsPerRow - 1) < -a1.w) continue;
-            const RowTerms rt = row_terms(a0.x, a0.y, a0.z, a1.x, ky);
-            if (rt.e2sq > a1.y) continue;  // whole row outside (s >= e2^2 for every pixel of it)
-            const float4 a2 = s2[j];
-            float sq[kStrip], lg[kStrip];
-            strip_exponents<kStrip>(a0.w, rt.e10, rt.e2sq, a1.z, sx, sq, lg);
-#pragma unroll
-            for (int p = 0; p < kStrip; ++p) {
-                if (sq[p] <= a1.y) {
-                    const float a = kClamp ? fminf(fast_exp2(lg[p]), kAlphaMax) : fast_exp2(lg[p]);
-                    const float2 aa = make_float2(a, a);
-                    b01[p] = __ffma2_rn(aa, make_float2(a2.x, a2.y), b01[p]);
-                    b2q[p] = __ffma2_rn(aa, make_float2(a2.z, a2.w), b2q[p]);
-                    if (kMode == kRasterSums)
-                        bl[p] = fmaf(ssign[j], log1pf(-a), bl[p]);
-                    else
-                        T[p] = fmaf(-T[p], a, T[p]);
-                    if (kCount) n_contrib += (tx * kTile + sx + p < vd.W && ty * kTile + ky < vd.H) ? 1u : 0u;
-                }
-            }
+        const int je = min(cnt, jb + 32);
+        for (int i = jb; i < je; i += 2) {
+            const int jA = list[i], jB = i + 1 < je ? list[i + 1] : kFwdBatch;
+            fwd_splat<kMode, kCount, kStrip, kTest, kClamp>(s0, s1, s2, ssign, jA, ky, sx, in_view_row, x0, W, b01,
+                                                            b2q, bl, T, n_contrib);
+            fwd_splat<kMode, kCount, kStrip, kTest, kClamp>(s0, s1, s2, ssign, jB, ky, sx, in_view_row, x0, W, b01,
+                                                            b2q, bl, T, n_contrib);
         }
 #pragma unroll
         for (int p = 0; p < kStrip; ++p) {
@@ -118,6 +110,17 @@ __device__ __forceinline__ void fwd_batch(const float4 *s0, const float4 *s1, co
             if (kMode == kRasterSums) T[p] += bl[p];
         }
     }
+}
+
+// Append the staging lanes whose flag is set to a shared list (warp ballot,
+// one shared atomic per warp).
+__device__ __forceinline__ void list_append(bool flag, int k, int *cnt, uint16_t *list) {
+    const int lane = threadIdx.x & 31;
+    const unsigned bal = __ballot_sync(0xffffffffu, flag);
+    int wb = 0;
+    if (lane == 0 && bal) wb = atomicAdd(cnt, __popc(bal));
+    wb = __shfl_sync(0xffffffffu, wb, 0);
+    if (flag) list[wb + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)k;
 }
 
 template <int kMode, bool kCount, int kStrip>
@@ -129,9 +132,15 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
                                                                  float *loss, unsigned long long *contrib) {
     constexpr int kFwdThreads = kTilePix / kStrip;
     constexpr int kStripsPerRow = kTile / kStrip;
-    __shared__ float4 s0[kFwdBatch], s1[kFwdBatch], s2[kFwdBatch];
-    __shared__ float ssign[kMode == kRasterSums ? kFwdBatch : 1];
-    __shared__ uint8_t sfl[kFwdBatch];  // 1: the splat's cutoff ellipse contains the whole tile
+    constexpr int kWarps = kFwdThreads / 32;
+    constexpr int kRowsPerWarp = kTile / kWarps;
+    // staged records; index kFwdBatch is an empty record (alpha 0 at every pixel)
+    __shared__ float4 s0[kFwdBatch + 1], s1[kFwdBatch + 1], s2[kFwdBatch + 1];
+    __shared__ float ssign[kMode == kRasterSums ? kFwdBatch + 1 : 1];
+    // per batch: the records whose cutoff ellipse contains the whole tile (every warp takes them
+    // without cutoff tests), and per warp the other records whose ellipse reaches its rows
+    __shared__ uint16_t flist[kFwdBatch], wlist[kWarps][kFwdBatch];
+    __shared__ int fcnt, wcnt[kWarps];
     __shared__ float red[kFwdThreads / 32];
     __shared__ unsigned red_n[kFwdThreads / 32];
 
@@ -140,13 +149,21 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
     const ViewDesc &vd = b.v[v];
     const int lt = gt - vd.tile_base;
     const int ty = lt / vd.tiles_x, tx = lt - ty * vd.tiles_x;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int ky = tid / kStripsPerRow, sx = (tid % kStripsPerRow) * kStrip;
-    const int wrow = (tid >> 5) * (32 / kStripsPerRow);  // first tile row of this warp
     const float ox = (float)(tx * kTile) + 0.5f, oy = (float)(ty * kTile) + 0.5f;
+    const bool in_view_row = ty * kTile + ky < vd.H;
+    const int x0 = tx * kTile + sx;
 
     const int start = offsets[gt];
     const int end = (int)min((int64_t)offsets[gt + 1], cap);
+
+    if (tid == 0) {
+        s0[kFwdBatch] = make_float4(0.f, 0.f, 0.f, 0.f);
+        s1[kFwdBatch] = make_float4(0.f, -INFINITY, -INFINITY, -1.f);  // log2 o = -inf: alpha 0
+        s2[kFwdBatch] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (kMode == kRasterSums) ssign[kFwdBatch] = 0.f;
+    }
 
     // per pixel: (P_r, P_g) and (P_b, Q) as f32x2 pairs (one paired FMA per pair of sums;
     // each component rounds like the scalar FMA), T (log T in sums mode)
@@ -161,50 +178,74 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
 
     for (int base = start; base < end; base += kFwdBatch) {
         const int n = min(kFwdBatch, end - base);
+        __syncthreads();  // the previous batch's records and lists are consumed
+        if (tid == 0) fcnt = 0;
+        if (tid < kWarps) wcnt[tid] = 0;
         __syncthreads();
         int may_clamp = 0;  // some staged splat can reach the 0.99 clamp
-        for (int k = tid; k < n; k += kFwdThreads) {
-            const uint32_t q = pairs[base + k];
+        for (int k0 = 0; k0 < n; k0 += kFwdThreads) {  // uniform trip count: the lists use warp ballots
+            const int k = k0 + tid;
             // staged: s0 = (A2 dx0, dy0, r A2, A2), s1 = (B2, thr, log2 o, yh),
             //         s2 = (w c_r, w c_g, w c_b, w) (times the sign in sums mode)
-            float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = make_float4(0.f, -INFINITY, 0.f, -1.f);
-            float4 t2 = make_float4(0.f, 0.f, 0.f, 0.f);
-            bool full = false;
-            if (q < nrec) {  // never written by this call's scatter otherwise: contributes nothing
-                const float4 a0 = rec[3 * (int64_t)q + 0];
-                const float4 a1 = rec[3 * (int64_t)q + 1];
-                const float4 a2 = rec[3 * (int64_t)q + 2];
-                const SplatConsts c = splat_consts(ox, oy, a0.x, a0.y, a0.z, a0.w, a1.y);
-                t0 = make_float4(c.A2dx0, c.dy0, c.rA2, a0.w);
-                t1 = make_float4(a1.x, c.thr, a1.y, a1.w);
-                // the whole tile inside the cutoff ellipse: its four corner pixels are, by a margin
-                // (convexity; the margin keeps every pixel's rounded exponent below the cut)
-                const float lim = c.thr - fmaf(1e-3f, fabsf(c.thr), 1e-3f);
-                bool in = true;
+            bool ok = false, full = false;
+            float dy0 = 0.f, yh = -1.f;
+            if (k < n) {
+                const uint32_t q = pairs[base + k];
+                float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = make_float4(0.f, -INFINITY, 0.f, -1.f);
+                float4 t2 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (q < nrec) {  // never written by this call's scatter otherwise: contributes nothing
+                    const float4 a0 = rec[3 * (int64_t)q + 0];
+                    const float4 a1 = rec[3 * (int64_t)q + 1];
+                    const float4 a2 = rec[3 * (int64_t)q + 2];
+                    const SplatConsts c = splat_consts(ox, oy, a0.x, a0.y, a0.z, a0.w, a1.y);
+                    t0 = make_float4(c.A2dx0, c.dy0, c.rA2, a0.w);
+                    t1 = make_float4(a1.x, c.thr, a1.y, a1.w);
+                    // the whole tile inside the cutoff ellipse: its four corner pixels are, by a margin
+                    // (convexity; the margin keeps every pixel's rounded exponent below the cut)
+                    const float lim = c.thr - fmaf(1e-3f, fabsf(c.thr), 1e-3f);
+                    bool in = true;
 #pragma unroll
-                for (int cyy = 0; cyy < 2; ++cyy) {
-                    const RowTerms rt = row_terms(c.A2dx0, c.dy0, c.rA2, a1.x, cyy * (kTile - 1));
+                    for (int cyy = 0; cyy < 2; ++cyy) {
+                        const RowTerms rt = row_terms(c.A2dx0, c.dy0, c.rA2, a1.x, cyy * (kTile - 1));
 #pragma unroll
-                    for (int cxx = 0; cxx < 2; ++cxx)
-                        in = in && quad_s(col_e1(a0.w, rt.e10, cxx * (kTile - 1)), rt.e2sq) <= lim;
+                        for (int cxx = 0; cxx < 2; ++cxx)
+                            in = in && quad_s(col_e1(a0.w, rt.e10, cxx * (kTile - 1)), rt.e2sq) <= lim;
+                    }
+                    ok = true;
+                    full = in;
+                    dy0 = c.dy0;
+                    yh = a1.w;
+                    may_clamp |= a1.y > kNoClampLog2 ? 1 : 0;
+                    const float ws = kMode == kRasterSums ? a1.z * a2.w : a1.z;
+                    t2 = make_float4(ws * a2.x, ws * a2.y, ws * a2.z, ws);
+                    if (kMode == kRasterSums) ssign[k] = a2.w;
                 }
-                full = in;
-                may_clamp |= a1.y > kNoClampLog2 ? 1 : 0;
-                const float ws = kMode == kRasterSums ? a1.z * a2.w : a1.z;
-                t2 = make_float4(ws * a2.x, ws * a2.y, ws * a2.z, ws);
+                s0[k] = t0;
+                s1[k] = t1;
+                s2[k] = t2;
             }
-            s0[k] = t0;
-            s1[k] = t1;
-            s2[k] = t2;
-            sfl[k] = full ? 1 : 0;
-            if (kMode == kRasterSums) ssign[k] = q < nrec ? rec[3 * (int64_t)q + 2].w : 0.f;
+            list_append(ok && full, k, &fcnt, flist);
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                // the ellipse's rows |dy0 + ky| <= yh reach rows [w R, w R + R - 1] of the tile
+                const float dlo = dy0 + (float)(w * kRowsPerWarp);
+                const bool hit = ok && !full && !(dlo > yh || dlo + (float)(kRowsPerWarp - 1) < -yh);
+                list_append(hit, k, &wcnt[w], wlist[w]);
+            }
         }
-        if (__syncthreads_or(may_clamp))
-            fwd_batch<kMode, kCount, kStrip, true>(s0, s1, s2, ssign, sfl, n, ky, sx, wrow, tx, ty, vd, P01, P2Q, T,
-                                                   n_contrib);
-        else
-            fwd_batch<kMode, kCount, kStrip, false>(s0, s1, s2, ssign, sfl, n, ky, sx, wrow, tx, ty, vd, P01, P2Q, T,
-                                                    n_contrib);
+        const bool clamp = __syncthreads_or(may_clamp) != 0;
+        const int nf = fcnt, nw = wcnt[warp];
+        if (clamp) {
+            fwd_list<kMode, kCount, kStrip, false, true>(s0, s1, s2, ssign, flist, nf, ky, sx, in_view_row, x0, vd.W,
+                                                         P01, P2Q, T, n_contrib);
+            fwd_list<kMode, kCount, kStrip, true, true>(s0, s1, s2, ssign, wlist[warp], nw, ky, sx, in_view_row, x0,
+                                                        vd.W, P01, P2Q, T, n_contrib);
+        } else {
+            fwd_list<kMode, kCount, kStrip, false, false>(s0, s1, s2, ssign, flist, nf, ky, sx, in_view_row, x0,
+                                                          vd.W, P01, P2Q, T, n_contrib);
+            fwd_list<kMode, kCount, kStrip, true, false>(s0, s1, s2, ssign, wlist[warp], nw, ky, sx, in_view_row, x0,
+                                                         vd.W, P01, P2Q, T, n_contrib);
+        }
     }
 
     const int64_t HW = (int64_t)vd.W * vd.H;
