@@ -153,16 +153,21 @@ __device__ __forceinline__ void bwd_rows(const BwdSplat &bs, const BwdState &S, 
 }
 
 constexpr int kBwdQuads = 2;  // groups of four pixels per warp vote
+// Threads per block (one block per tile).  Each round gives every warp 32 of the tile's splats;
+// four warps keep more of a typical tile's warps busy (the median tile holds ~110 splats at a 5 %
+// active set) than eight, without stretching the heaviest tiles into long serial chains as two do.
+constexpr int kBwdThreads = 128;
+constexpr int kBwdMinBlocks = 12 * 64 / kBwdThreads;  // <= 85 registers a thread
 
 template <bool kGroup>
-__global__ void __launch_bounds__(kTilePix, 3) raster_bwd_kernel(const __grid_constant__ Batch b,
+__global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) raster_bwd_kernel(const __grid_constant__ Batch b,
                                                               const float4 *__restrict__ rec,
                                                               const int *__restrict__ offsets,
                                                               const uint32_t *__restrict__ pairs, int64_t cap,
                                                               uint32_t nrec, float4 *__restrict__ sgrad) {
     __shared__ BwdState S;
-    __shared__ uint32_t sorted[kGroup ? kTilePix : 1];
-    __shared__ uint8_t sfull[kGroup ? kTilePix : 1];
+    __shared__ uint32_t sorted[kGroup ? kBwdThreads : 1];
+    __shared__ uint8_t sfull[kGroup ? kBwdThreads : 1];
     __shared__ int hist[kBwdKeys];
 
     const int gt = block_tile(b);
@@ -171,8 +176,9 @@ __global__ void __launch_bounds__(kTilePix, 3) raster_bwd_kernel(const __grid_co
     const int lt = gt - vd.tile_base;
     const int ty = lt / vd.tiles_x, tx = lt - ty * vd.tiles_x;
     const int tid = threadIdx.x;
-    {
-        const int x = tx * kTile + (tid & (kTile - 1)), y = ty * kTile + (tid >> 4);
+#pragma unroll
+    for (int t = tid; t < kTilePix; t += kBwdThreads) {
+        const int x = tx * kTile + (t & (kTile - 1)), y = ty * kTile + (t >> 4);
         float st5[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
         if (x < vd.W && y < vd.H) {
             const int64_t HW = (int64_t)vd.W * vd.H, pix = (int64_t)y * vd.W + x;
@@ -181,7 +187,7 @@ __global__ void __launch_bounds__(kTilePix, 3) raster_bwd_kernel(const __grid_co
             for (int k = 0; k < 5; ++k) st5[k] = st[k * HW + pix];
         }
 #pragma unroll
-        for (int k = 0; k < 5; ++k) reinterpret_cast<float *>(S.p[k])[tid] = st5[k];
+        for (int k = 0; k < 5; ++k) reinterpret_cast<float *>(S.p[k])[t] = st5[k];
     }
     __syncthreads();
 
@@ -190,7 +196,7 @@ __global__ void __launch_bounds__(kTilePix, 3) raster_bwd_kernel(const __grid_co
     const int warp = tid >> 5, lane = tid & 31;
     const float ox = (float)(tx * kTile) + 0.5f, oy = (float)(ty * kTile) + 0.5f;
 
-    for (int cb0 = start; cb0 < end; cb0 += kTilePix) {
+    for (int cb0 = start; cb0 < end; cb0 += kBwdThreads) {
         uint32_t q;
         bool full = false;
         if (kGroup) {
@@ -198,7 +204,7 @@ __global__ void __launch_bounds__(kTilePix, 3) raster_bwd_kernel(const __grid_co
             // four corner pixels do, by a margin; the ellipse is convex, so then every pixel does
             // and its rounded exponent stays below the cut), classes 1-16 = the 4x4-pixel cell of
             // the centre (clamped), 17 = no record; then warps take 32 consecutive splats
-            const int nr = min(kTilePix, end - cb0);
+            const int nr = min(kBwdThreads, end - cb0);
             uint32_t myq = 0xffffffffu;
             int key = kBwdKeys - 1, slot = 0;
             if (tid < kBwdKeys) hist[tid] = 0;
@@ -335,9 +341,9 @@ int launch_raster_bwd(const Batch &b, bool group, const float4 *rec, const int *
     if (b.total_tiles == 0) return 0;
     const uint32_t nrec = (uint32_t)((int64_t)b.n_views * b.n_list);
     if (group)
-        raster_bwd_kernel<true><<<b.total_tiles, kTilePix, 0, st>>>(b, rec, offsets, pairs, cap, nrec, sgrad);
+        raster_bwd_kernel<true><<<b.total_tiles, kBwdThreads, 0, st>>>(b, rec, offsets, pairs, cap, nrec, sgrad);
     else
-        raster_bwd_kernel<false><<<b.total_tiles, kTilePix, 0, st>>>(b, rec, offsets, pairs, cap, nrec, sgrad);
+        raster_bwd_kernel<false><<<b.total_tiles, kBwdThreads, 0, st>>>(b, rec, offsets, pairs, cap, nrec, sgrad);
     return 0;
 }
 

@@ -23,6 +23,7 @@
 namespace soit {
 
 constexpr int kFwdBatch = 256;    // records staged per round
+constexpr int kFwdUnroll = 2;     // records per iteration of the accumulation loop
 
 // The strip's quadratics s = e1^2 + e2^2 and log2 alpha_raw = log2 o - s, two
 // pixels per f32x2 instruction where the strip has pairs (each component
@@ -80,9 +81,9 @@ __device__ __forceinline__ void fwd_splat(const float4 *s0, const float4 *s1, co
 }
 
 // A list of staged records (indices into the staged arrays) into the
-// thread's strip, two records per iteration (the odd one out pairs with the
-// empty record at index kFwdBatch), summed in 32-record blocks that are added
-// to the totals (two-level summation).
+// thread's strip, kFwdUnroll records per iteration (a short last iteration is
+// filled with the empty record at index kFwdBatch), summed in 32-record blocks
+// that are added to the totals (two-level summation).
 template <int kMode, bool kCount, int kStrip, bool kTest, bool kClamp>
 __device__ __forceinline__ void fwd_list(const float4 *s0, const float4 *s1, const float4 *s2, const float *ssign,
                                          const uint16_t *list, int cnt, int ky, int sx, bool in_view_row, int x0,
@@ -96,12 +97,13 @@ __device__ __forceinline__ void fwd_list(const float4 *s0, const float4 *s1, con
             bl[p] = 0.f;
         }
         const int je = min(cnt, jb + 32);
-        for (int i = jb; i < je; i += 2) {
-            const int jA = list[i], jB = i + 1 < je ? list[i + 1] : kFwdBatch;
-            fwd_splat<kMode, kCount, kStrip, kTest, kClamp>(s0, s1, s2, ssign, jA, ky, sx, in_view_row, x0, W, b01,
-                                                            b2q, bl, T, n_contrib);
-            fwd_splat<kMode, kCount, kStrip, kTest, kClamp>(s0, s1, s2, ssign, jB, ky, sx, in_view_row, x0, W, b01,
-                                                            b2q, bl, T, n_contrib);
+        for (int i = jb; i < je; i += kFwdUnroll) {
+#pragma unroll
+            for (int u = 0; u < kFwdUnroll; ++u) {
+                const int j = i + u < je ? list[i + u] : kFwdBatch;
+                fwd_splat<kMode, kCount, kStrip, kTest, kClamp>(s0, s1, s2, ssign, j, ky, sx, in_view_row, x0, W,
+                                                                b01, b2q, bl, T, n_contrib);
+            }
         }
 #pragma unroll
         for (int p = 0; p < kStrip; ++p) {
