@@ -93,12 +93,13 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Ba
     q[0] = q4.x; q[1] = q4.y; q[2] = q4.z; q[3] = q4.w;
     for (int j = 0; j < 3; ++j) ls[j] = __ldg(sp.log_scales + 3 * (int64_t)i + j);
     const float ol = __ldg(sp.opacity_logits + i);
-    const float o = 1.f / (1.f + expf(-ol));
-    const float log2o = log2f(o);
+    // every load of the row is issued before the first arithmetic that waits on one
     const ShT *hc = reinterpret_cast<const ShT *>(sp.sh_color) + 48 * (int64_t)i;
     const ShT *hw = reinterpret_cast<const ShT *>(sp.sh_weight) + 16 * (int64_t)i;
     float h0[J], h1[J], h2[J], hv[J];
     load_sh_run<ShT, J>(hc, hw, J * k, h0, h1, h2, hv);
+    const float o = 1.f / (1.f + expf(-ol));
+    const float log2o = log2f(o);
 
     for (int v = 0; v < b.n_views; ++v) {
         const ViewDesc &vd = b.v[v];
@@ -199,6 +200,10 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(const int *__restrict_
                                                           int *__restrict__ offsets, int *__restrict__ cursor,
                                                           int *__restrict__ order, int64_t cap, unsigned *status,
                                                           int64_t *pairs_out) {
+    // one chunk of 8192 counts at a time, staged through shared memory so that the global loads
+    // and stores are coalesced; element e sits at e + e / 32 (thread t's eight consecutive elements
+    // then fall in distinct banks across the warp)
+    __shared__ int sv[8192 + 8192 / 32];
     __shared__ int warp_sums[32];
     __shared__ int carry_s;
     __shared__ int cls_pos[kLoadClasses];
@@ -206,12 +211,15 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(const int *__restrict_
     if (tid == 0) carry_s = 0;
     __syncthreads();
     for (int base = 0; base < total; base += 1024 * 8) {
+        const int nb = min(1024 * 8, total - base);
+        for (int i = tid; i < 1024 * 8; i += 1024) sv[i + (i >> 5)] = i < nb ? count[base + i] : 0;
+        __syncthreads();
         int vals[8];
         int local = 0;
-        const int i0 = base + tid * 8;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            vals[k] = (i0 + k < total) ? count[i0 + k] : 0;
+            const int e = tid * 8 + k;
+            vals[k] = sv[e + (e >> 5)];
             local += vals[k];
         }
         int incl = local;
@@ -237,13 +245,16 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(const int *__restrict_
         int run = carry + warp_sums[warp] + incl - local;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            if (i0 + k < total) {
-                offsets[i0 + k] = run;
-                cursor[i0 + k] = run;
-            }
+            const int e = tid * 8 + k;
+            sv[e + (e >> 5)] = run;
             run += vals[k];
         }
         __syncthreads();
+        for (int i = tid; i < nb; i += 1024) {
+            const int o = sv[i + (i >> 5)];
+            offsets[base + i] = o;
+            cursor[base + i] = o;
+        }
         if (tid == 1023) carry_s = run;
         __syncthreads();
     }
@@ -287,7 +298,7 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(const int *__restrict_
 // entry's tile list, and each lane then takes one (row, column) of it, so a
 // typical splat costs one round of position-returning atomics instead of one
 // per row.
-__global__ void __launch_bounds__(256, 4) scatter_kernel(const __grid_constant__ Batch b,
+__global__ void __launch_bounds__(256, 8) scatter_kernel(const __grid_constant__ Batch b,
                                                          const float4 *__restrict__ rec,
                                                          const float4 *__restrict__ ext, int *__restrict__ cursor,
                                                          uint32_t *__restrict__ pairs, int64_t cap) {
@@ -297,12 +308,13 @@ __global__ void __launch_bounds__(256, 4) scatter_kernel(const __grid_constant__
     for (int v = 0; v < b.n_views; ++v) {
         const ViewDesc &vd = b.v[v];
         const int64_t qidx = (int64_t)v * b.n_list + r;
+        // the three loads are issued together (the record is read even when the splat is culled)
         const float4 e = ext[qidx];
+        const float4 r0 = rec[3 * qidx + 0];
+        const float B2 = rec[3 * qidx + 1].x;
         int ty0, ty1;
         if (!(e.x > 0.f)) continue;
-        const float4 r0 = rec[3 * qidx + 0];
         if (!tile_rows(vd, r0.y, e, ty0, ty1)) continue;
-        const float B2 = rec[3 * qidx + 1].x;
         for (int tyb = ty0; tyb <= ty1; tyb += 32) {
             const int ty = tyb + lane;
             int tx0 = 0, cnt = 0;
