@@ -74,7 +74,7 @@ __device__ __forceinline__ bool row_tiles(const ViewDesc &vd, float mx, float my
 // cutoff ellipse are counted by the lanes in parallel.  List entry r < n1 is
 // splat list1[r] with sign +1, r >= n1 is splat list2[r - n1] with sign -1.
 template <typename ShT, int G>
-__global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Batch b, SplatPtrs sp,
+__global__ void __launch_bounds__(256, 3) project_kernel(const __grid_constant__ Batch b, SplatPtrs sp,
                                                       const int *__restrict__ list1, int n1,
                                                       const int *__restrict__ list2, int n2, float4 *__restrict__ rec,
                                                       float4 *__restrict__ ext, int *__restrict__ tile_count) {

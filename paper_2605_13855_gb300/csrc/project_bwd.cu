@@ -10,7 +10,7 @@
 namespace soit {
 
 template <typename ShT>
-__global__ void __launch_bounds__(128) project_bwd_kernel(const __grid_constant__ Batch b, SplatPtrs sp,
+__global__ void __launch_bounds__(128, 3) project_bwd_kernel(const __grid_constant__ Batch b, SplatPtrs sp,
                                                           const int *__restrict__ list, int n,
                                                           const float4 *__restrict__ sgrad, GradPtrs out) {
     __shared__ float red[4];
