@@ -2,7 +2,7 @@
 //
 // Per-splat parallel: a tile's 256 pixel states are loaded into shared
 // memory once; each warp takes 32 of the tile's splats (lane = splat) and
-// walks all 256 pixels, reading each pixel's state as a shared-memory
+// walks the tile's pixels, reading each pixel's state as a shared-memory
 // broadcast.  Nothing is stored per pixel in the forward except the state,
 // the per-pair alpha is recomputed from the same record, and each lane ends
 // the tile with its splat's full tile gradient in registers, added with one
@@ -30,7 +30,7 @@ namespace soit {
 // (the dy sums taken per tile row, where dy is constant) gives
 //   dL/dmu'x = -K A2 Se,  dL/dmu'y = K (A2 r Se - B2^2 Sdy),
 //   dL/dr = -K A2 Sey,    dL/dA2 = K See / A2,  dL/dB2 = K B2 Sdyy.
-// kGroup: before a round of 256 of the tile's splats is split into warps, a
+// kGroup: before a round of the tile's splats (one per thread) is split into warps, a
 // shared-memory counting sort puts first the splats whose cutoff ellipse
 // contains the whole tile, then the others by the 4x4-pixel cell of the tile
 // that holds their centre (clamped).  A warp whose splats all contain the

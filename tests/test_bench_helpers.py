@@ -47,3 +47,11 @@ def test_recorded_traffic_follows_the_source_digest(tmp_path, monkeypatch):
     assert bench.recorded_traffic("raster_bwd") == 12345.0
     assert bench.recorded_traffic("raster_fwd") is None  # recorded for other sources
     assert bench.recorded_traffic("project_bwd") is None  # not recorded
+
+
+def test_digest_ignores_comments_but_not_code():
+    src = "// header\nint f(int x) {  /* block\n comment */\n    return x + 1;  // trailing\n}\n\n"
+    same = "int f(int x) {\n    return x + 1;\n}\n"
+    other = "int f(int x) {\n    return x + 2;\n}\n"
+    assert bench._code_only(src) == bench._code_only(same)
+    assert bench._code_only(src) != bench._code_only(other)
