@@ -190,6 +190,30 @@ def test_high_opacity_clamped_pairs():
     assert clamped > 0  # some pairs were clamped at 0.99
 
 
+@pytest.mark.parametrize("strip", [1, 2, 4])
+def test_counted_evaluations_match_the_oracle(strip):
+    """The counting pass of the forward raster (the E of the benchmark's
+    evals/s) counts exactly the active (splat, pixel) pairs inside the view
+    whose alpha reaches 1/255, for every strip width, with splats that cover
+    whole tiles (the untested list) among ordinary ones."""
+    n = 6000
+    scene = scenes.clustered_scene(n, 5100)
+    scene["log_scales"][:40] += 2.0
+    cam = scenes.random_camera(5103, 133, 101)
+    mask = scenes.random_active_mask(n, 0.5, 5102)
+    sp = SplatParams.from_numpy(scene)
+    r = Renderer(n, [(cam["width"], cam["height"])], fwd_pixels_per_thread=strip)
+    r.set_active(torch.as_tensor(mask, device="cuda"))
+    r.commit_frozen(sp, cam, 0)
+    r.set_counting(True)
+    r.forward(sp, [cam], [0])
+    r.status()
+    _, E = r.last_counts()
+    _, _, stats = oracle.render_sums(scene, cam, subset=mask.astype(bool))
+    # FP32 and FP64 may decide a pair within rounding of the 1/255 cut differently
+    assert abs(E - int(stats[0])) <= max(2, 1e-4 * int(stats[0])), (E, int(stats[0]))
+
+
 def test_multiview_batch_equals_single_views():
     n = 8000
     scene = scenes.unbounded_scene(n, 3100)
