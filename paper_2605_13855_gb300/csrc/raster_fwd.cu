@@ -2,9 +2,12 @@
 //
 // One block per 16x16 tile; each thread owns a 1xS strip of pixels of one
 // row (S = 1, 2 or 4, a launch parameter; the exponent of the next pixel of
-// the strip costs one FMA), each warp owns 2S rows and skips, warp-uniformly,
-// splats whose cutoff ellipse misses those rows.  The tile's records are staged through shared
-// memory 256 at a time, already shifted to tile-relative offsets.  Every
+// the strip costs one FMA), each warp owns 2S rows.  The tile's records are
+// staged through shared memory 256 at a time, already shifted to
+// tile-relative offsets, and sorted by warp ballots into one list of the
+// records whose cutoff ellipse contains the whole tile (evaluated without
+// cutoff tests) and, per warp, a list of the other records that reach its
+// rows; each warp walks its lists two records per branch-free iteration.  Every
 // pixel accumulates over the tile's splats P += a w c, Q += a w and
 // T *= (1 - a) (log T += log(1 - a) for the frozen sums), the sums taken in
 // 32-splat blocks added to the total, so that the FP32 rounding of sums over
