@@ -196,6 +196,19 @@ int sparseoit_commit_frozen(sparseoit_ctx *ctx, const sparseoit_splats *splats, 
  * (P_r, P_g, P_b, Q, log T).  Valid until destroy. */
 int sparseoit_get_frozen(sparseoit_ctx *ctx, int32_t view, float **d_planes);
 
+/* Sec. 4.1 keeps the pre-rendered sums of the inactive splats as the only
+ * state that outlives an iteration; this restores them (checkpoint and
+ * resume).  planes: 5 planes of H*W floats in the layout of
+ * sparseoit_get_frozen, in device or host memory (copied with
+ * cudaMemcpyDefault on `stream`; the caller keeps ownership).  The view is
+ * then treated as committed under the current active set: the caller
+ * guarantees that the planes are the sums of the complement of that set
+ * (for example saved by sparseoit_get_frozen under the same mask) for the
+ * current parameters of the complement, sigma, c0 and the view's camera.
+ * ERR_STATE before the first set_active; ERR_INVALID_ARG for a bad view or
+ * a null pointer; ERR_CUDA if the copy cannot be enqueued. */
+int sparseoit_set_frozen(sparseoit_ctx *ctx, int32_t view, const float *planes, void *stream);
+
 /* Alg. 1 / Alg. 2 (BAN): render the active set of n_views views in one
  * batched launch sequence and compose each with its frozen sums (Eq. 7).
  *   cams[k] (host) is the camera of view views[k] (host int array);

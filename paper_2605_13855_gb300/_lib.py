@@ -33,7 +33,8 @@ ERROR_NAMES = {ERR_INVALID_ARG: "INVALID_ARG", ERR_OOM: "OOM", ERR_CUDA: "CUDA",
 # Every entry point declared in include/sparseoit.h.
 EXPORTED = (
     "sparseoit_create", "sparseoit_destroy", "sparseoit_set_active", "sparseoit_get_active",
-    "sparseoit_commit_frozen", "sparseoit_get_frozen", "sparseoit_forward", "sparseoit_backward",
+    "sparseoit_commit_frozen", "sparseoit_get_frozen", "sparseoit_set_frozen", "sparseoit_forward",
+    "sparseoit_backward",
     "sparseoit_reserve_pairs", "sparseoit_status", "sparseoit_last_counts", "sparseoit_set_counting",
     "sparseoit_set_profiling", "sparseoit_get_profile", "sparseoit_last_error", "sparseoit_version",
     "sparseoit_compact_active_static", "sparseoit_autotune", "sparseoit_fps_views", "sparseoit_activeness",
@@ -112,6 +113,7 @@ def load(path: str = LIB_PATH):
             "sparseoit_get_active": ([vp, P(vp), P(i64)], ctypes.c_int),
             "sparseoit_commit_frozen": ([vp, P(Splats), P(Camera), i32, i32, vp], ctypes.c_int),
             "sparseoit_get_frozen": ([vp, i32, P(vp)], ctypes.c_int),
+            "sparseoit_set_frozen": ([vp, i32, vp, vp], ctypes.c_int),
             "sparseoit_forward": ([vp, P(Splats), P(Camera), P(i32), i32, P(vp), P(vp), vp, vp], ctypes.c_int),
             "sparseoit_backward": ([vp, P(Splats), P(vp), P(Grads), vp], ctypes.c_int),
             "sparseoit_reserve_pairs": ([vp, i64], ctypes.c_int),

@@ -12,9 +12,23 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/sparseoit.h"
 #include "common.cuh"
 #include "launch.h"
+
+namespace {
+// A named NVTX range around each entry point that enqueues GPU work, so that a
+// profiler timeline shows the library's calls (header-only NVTX; inert when no
+// tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
 
 using namespace soit;
 
@@ -371,6 +385,7 @@ int sparseoit_destroy(sparseoit_ctx *ctx) {
 }
 
 int sparseoit_set_active(sparseoit_ctx *ctx, const uint8_t *d_mask, int64_t n, void *stream) {
+    NvtxRange nvtx__("sparseoit_set_active");
     if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
     if (!d_mask && n > 0) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "mask is null");
     if (n != ctx->N) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "mask length differs from max_splats");
@@ -412,8 +427,22 @@ int sparseoit_get_frozen(sparseoit_ctx *ctx, int32_t view, float **d_planes) {
     return SPARSEOIT_OK;
 }
 
+int sparseoit_set_frozen(sparseoit_ctx *ctx, int32_t view, const float *planes, void *stream) {
+    NvtxRange nvtx__("sparseoit_set_frozen");
+    if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
+    if (!planes) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "null frozen planes");
+    if (view < 0 || view >= ctx->n_views) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "view index out of range");
+    if (!ctx->have_mask) return fail(ctx, SPARSEOIT_ERR_STATE, "set_frozen before set_active");
+    const size_t bytes = (size_t)5 * (size_t)ctx->W[view] * (size_t)ctx->H[view] * sizeof(float);
+    CK(cudaMemcpyAsync(ctx->d_frozen[view], planes, bytes, cudaMemcpyDefault, (cudaStream_t)stream),
+       "cudaMemcpyAsync(frozen planes)");
+    ctx->view_gen[view] = ctx->generation;
+    return SPARSEOIT_OK;
+}
+
 int sparseoit_commit_frozen(sparseoit_ctx *ctx, const sparseoit_splats *splats, const sparseoit_camera *cam,
                             int32_t view, int32_t mode, void *stream) {
+    NvtxRange nvtx__("sparseoit_commit_frozen");
     if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
     int rc = check_splats(ctx, splats, false);
     if (rc) return rc;
@@ -539,11 +568,13 @@ static int forward_impl(sparseoit_ctx *ctx, const sparseoit_splats *splats, cons
 int sparseoit_forward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const sparseoit_camera *cams,
                       const int32_t *views, int32_t n_views, float *const *d_images, const float *const *d_targets,
                       float *d_loss, void *stream) {
+    NvtxRange nvtx__("sparseoit_forward");
     return forward_impl(ctx, splats, cams, views, n_views, d_images, d_targets, d_loss, stream, false);
 }
 
 int sparseoit_backward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const float *const *d_grad_images,
                        sparseoit_grads *out, void *stream) {
+    NvtxRange nvtx__("sparseoit_backward");
     if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
     int rc = check_splats(ctx, splats, true);
     if (rc) return rc;
@@ -598,6 +629,7 @@ int sparseoit_update_active_set(sparseoit_ctx *ctx, const sparseoit_splats *spla
                                 int32_t n_views, const float *const *d_targets, int32_t n_sub, int32_t first,
                                 const float *eps, sparseoit_grads *scratch, uint8_t *d_mask, int32_t *sel_out,
                                 void *stream) {
+    NvtxRange nvtx__("sparseoit_update_active_set");
     if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
     if (!splats || !cams || !d_targets || !eps || !scratch || !d_mask)
         return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "update_active_set: null argument");
@@ -636,6 +668,7 @@ int sparseoit_update_active_set(sparseoit_ctx *ctx, const sparseoit_splats *spla
 
 int sparseoit_adam_step(sparseoit_ctx *ctx, const sparseoit_grads *grads, sparseoit_rows *params, sparseoit_rows *m,
                         sparseoit_rows *v, const sparseoit_adam *cfg, void *stream) {
+    NvtxRange nvtx__("sparseoit_adam_step");
     if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
     if (!grads || !params || !m || !v || !cfg) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "adam: null argument");
     if (!ctx->have_mask) return fail(ctx, SPARSEOIT_ERR_STATE, "adam before set_active");
@@ -695,6 +728,7 @@ int sparseoit_adam_step(sparseoit_ctx *ctx, const sparseoit_grads *grads, sparse
 
 int sparseoit_loss_l1_dssim(sparseoit_ctx *ctx, const float *const *d_targets, float lambda, float *d_loss,
                             float *const *d_grad_images, const float *bg, void *stream) {
+    NvtxRange nvtx__("sparseoit_loss_l1_dssim");
     if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
     if (!d_targets || !d_loss || !bg) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "loss: null argument");
     if (!(lambda >= 0.f && lambda <= 1.f)) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "loss: lambda outside [0, 1]");
@@ -771,6 +805,7 @@ int sparseoit_scatter_active(sparseoit_ctx *ctx, const sparseoit_rows *active, s
 int sparseoit_autotune(sparseoit_ctx *ctx, const sparseoit_splats *splats, const sparseoit_camera *cams,
                        const int32_t *views, int32_t n_views, float *const *d_images, const float *const *d_targets,
                        float *d_loss, int32_t reps, sparseoit_tuning *out, void *stream) {
+    NvtxRange nvtx__("sparseoit_autotune");
     if (!ctx || !out) return SPARSEOIT_ERR_INVALID_ARG;
     if (reps < 1) reps = 3;
     cudaStream_t st = (cudaStream_t)stream;

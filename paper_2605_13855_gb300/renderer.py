@@ -185,6 +185,15 @@ class Renderer:
         W, H = self.view_sizes[view]
         return torch.as_tensor(_DeviceArray(p.value, (5, H, W), "<f4"), device="cuda").clone()
 
+    def set_frozen(self, view: int, planes: torch.Tensor, stream=None):
+        """Restore a view's frozen sums ([5, H, W] float32, device or host, contiguous), e.g. saved by
+        frozen_sums() under the same active set: checkpoint and resume without a recompute."""
+        W, H = self.view_sizes[view]
+        if planes.dtype != torch.float32 or tuple(planes.shape) != (5, H, W) or not planes.is_contiguous():
+            raise ValueError(f"frozen planes must be contiguous float32 [5, {H}, {W}]")
+        self._check(self.lib.sparseoit_set_frozen(self._ctx, int(view), ctypes.c_void_p(planes.data_ptr()),
+                                                  ctypes.c_void_p(_stream_ptr(stream))))
+
     def commit_frozen(self, splats: SplatParams, cam: dict, view: int, mode: str = "incremental", stream=None):
         """Sec. 4.1 / Alg. 2 BAU: bring the view's frozen sums up to date."""
         m = _lib.COMMIT_INCREMENTAL if mode == "incremental" else _lib.COMMIT_RECOMPUTE

@@ -1,11 +1,13 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
 
 import oracle
 from paper_2605_13855_gb300 import scenes
-from paper_2605_13855_gb300._lib import ERR_CAPACITY, ERR_STATE, SparseOITError
+from paper_2605_13855_gb300._lib import ERR_CAPACITY, ERR_INVALID_ARG, ERR_STATE, SparseOITError
 from paper_2605_13855_gb300.renderer import Renderer, SparseOITRender, SplatParams
 from tests.parity_util import AMB_BAND, AMB_PIX_MAX, GRAD_TOL, IMG_TOL, check_against_oracle, image_error, \
     oracle_grads, to_np
@@ -212,6 +214,55 @@ def test_counted_evaluations_match_the_oracle(strip):
     _, _, stats = oracle.render_sums(scene, cam, subset=mask.astype(bool))
     # FP32 and FP64 may decide a pair within rounding of the 1/255 cut differently
     assert abs(E - int(stats[0])) <= max(2, 1e-4 * int(stats[0])), (E, int(stats[0]))
+
+
+def test_set_frozen_restores_a_checkpoint():
+    """The frozen sums saved from one context and restored into a fresh one
+    (device or host copy) give the same active render as a recompute, and
+    the restore is refused before set_active or for a bad view."""
+    n = 5000
+    scene = scenes.clustered_scene(n, 6100)
+    cam = scenes.random_camera(6103, 90, 70)
+    mask = scenes.random_active_mask(n, 0.2, 6102)
+    r, sp = _renderer_for(scene, [cam], mask)
+    saved = r.frozen_sums(0)
+    (img_ref,), _ = r.forward(sp, [cam], [0])
+    img_ref = to_np(img_ref)
+    scale = np.abs(img_ref).max()
+    for planes in (saved, saved.cpu()):
+        r2 = Renderer(n, [(cam["width"], cam["height"])])
+        with pytest.raises(SparseOITError) as ei:
+            r2.set_frozen(0, planes)
+        assert ei.value.code == ERR_STATE
+        r2.set_active(torch.as_tensor(mask, device="cuda"))
+        rc = r2.lib.sparseoit_set_frozen(r2._ctx, 1, ctypes.c_void_p(planes.data_ptr()), None)  # no view 1
+        assert rc == ERR_INVALID_ARG
+        r2.set_frozen(0, planes)
+        (img,), _ = r2.forward(sp, [cam], [0])
+        r2.status()
+        assert np.abs(to_np(img) - img_ref).max() <= 1e-6 * scale
+        r2.close()
+
+
+def test_repeat_runs_agree():
+    """Two forward + backward passes over the same inputs agree to rounding
+    (only the order of a tile's pairs and of float atomics may differ)."""
+    scene, _, cam = scenes.tiny_workload()
+    n = scene["means"].shape[0]
+    mask = scenes.random_active_mask(n, 0.5, 11)
+    r, sp = _renderer_for(scene, [cam], mask)
+    g = torch.as_tensor(_linear_g(cam, 12), dtype=torch.float32, device="cuda")
+    runs = []
+    for _ in range(2):
+        (img,), _ = r.forward(sp, [cam], [0])
+        grads = r.backward(sp, [g])
+        r.status()
+        runs.append((to_np(img), {k: to_np(v) for k, v in grads.items()}))
+    (i0, g0), (i1, g1) = runs
+    assert np.abs(i0 - i1).max() <= 1e-6 * np.abs(i0).max()
+    for k in g0:
+        scale = max(np.abs(g0[k]).max(), 1e-30)
+        assert np.abs(g0[k] - g1[k]).max() <= 1e-5 * scale, k
 
 
 def test_multiview_batch_equals_single_views():
