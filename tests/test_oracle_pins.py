@@ -345,3 +345,129 @@ def test_gradient_matches_central_finite_differences(seed, opacity_shift):
         lm = _loss(sc, cam, g)
         sc["sigma"] = s0
         assert abs((lp - lm) / (2 * h) - dsig) <= 1e-6 * max(1.0, abs(dsig))
+
+
+# ------------------------------------------- clamps and the near plane ----
+
+def test_negative_colour_channel_is_clamped_to_zero():
+    """Eq. 4 with the max(0, .) activation: a channel whose SH value is below zero renders as a
+    zero colour, so a lone splat on the axis gives (1 - a) c0 in that channel and (1 - a) c0 + a c
+    in the others; that channel's coefficients get no gradient."""
+    cam = axis_camera(33, 33, f=100.0)
+    z, o, s = 3.0, 0.7, math.exp(-3.0)
+    sh = np.zeros((16, 3))
+    sh[0] = [-2.5, 0.3, 0.0]        # red: 0.5 - 2.5 Y00 = -0.205 < 0
+    shw = np.zeros(16)
+    shw[0] = 0.3
+    bg = (0.2, 0.4, 0.6)
+    sc = make_scene([[0, 0, z]], [[math.log(s)] * 3], [logit(o)], sh_color=[sh], sh_weight=[shw],
+                    sigma=6.0, bg=bg)
+    r = oracle.render(sc, cam)
+    c = 0.5 + sh[0] * _zonal(0)
+    assert c[0] < -0.1
+    c_act = np.maximum(c, 0.0)
+    var = (cam["fx"] * s / z) ** 2 + 0.3
+    for k in range(0, 6):
+        a = o * math.exp(-0.5 * k * k / var)
+        want = (1 - a) * np.array(bg) + a * c_act
+        assert np.allclose(r["image"][16, 16 + k], want, atol=1e-14, rtol=0)
+        assert r["sums"][0, 16, 16 + k] == 0.0
+    # gradient of a linear loss on the red channel only: the red SH is dead, green is not
+    g = np.zeros(r["image"].shape)
+    g[..., 0] = 1.0
+    g[..., 1] = 1.0
+    grads, _, _ = oracle.backward(sc, cam, r["sums"], g)
+    red = grads[0, 11:59].reshape(16, 3)[:, 0]
+    green = grads[0, 11:59].reshape(16, 3)[:, 1]
+    assert np.all(red == 0.0)
+    assert abs(green[0]) > 1e-3
+
+
+def test_negative_weight_sh_gives_zero_weight():
+    """Eq. 1 with v = max(0, SH + 0.5): a splat whose weight SH is below zero has w = 0.  It still
+    attenuates (T) but adds nothing to P or Q: alone it renders (1 - a) c0 (Q = 0, F := 0); beside a
+    positive-weight splat the normalised colour is the other splat's colour exactly."""
+    cam = axis_camera(17, 17, f=100.0)
+    o1, o2 = 0.6, 0.3
+    sh = np.zeros((2, 16, 3))
+    sh[0, 0] = [0.5, 0.0, -0.5]
+    sh[1, 0] = [-0.3, 0.6, 0.2]
+    shw = np.zeros((2, 16))
+    shw[0, 0] = -2.5                # v_raw = 0.5 - 2.5 Y00 < 0
+    shw[1, 0] = 0.2
+    bg = (0.3, 0.2, 0.1)
+    z = np.array([2.0, 4.0])
+    lone = make_scene([[0, 0, z[0]]], None, [logit(o1)], sh_color=sh[:1], sh_weight=shw[:1], sigma=5.0, bg=bg)
+    r = oracle.render(lone, cam)
+    assert r["sums"][3, 8, 8] == 0.0 and np.all(r["sums"][:3, 8, 8] == 0.0)
+    assert np.allclose(r["image"][8, 8], (1 - o1) * np.array(bg), atol=1e-15, rtol=0)
+    both = make_scene([[0, 0, z[0]], [0, 0, z[1]]], None, [logit(o1), logit(o2)], sh_color=sh, sh_weight=shw,
+                      sigma=5.0, bg=bg)
+    img = oracle.render(both, cam)["image"][8, 8]
+    c2 = 0.5 + sh[1, 0] * _zonal(0)
+    T = (1 - o1) * (1 - o2)
+    assert np.allclose(img, T * np.array(bg) + (1 - T) * c2, atol=1e-14, rtol=0)
+    # the clamped weight SH gets no gradient; the same splat with a positive weight does
+    rb = oracle.render(both, cam)
+    grads, _, _ = oracle.backward(both, cam, rb["sums"], np.ones(rb["image"].shape))
+    assert np.all(grads[0, 59:75] == 0.0)
+    live = make_scene([[0, 0, z[0]], [0, 0, z[1]]], None, [logit(o1), logit(o2)], sh_color=sh,
+                      sh_weight=np.abs(shw) * 0.1, sigma=5.0, bg=bg)
+    rl = oracle.render(live, cam)
+    gl, _, _ = oracle.backward(live, cam, rl["sums"], np.ones(rl["image"].shape))
+    assert abs(gl[0, 59]) > 1e-3
+
+
+@pytest.mark.parametrize("tz,visible", [(0.19, False), (0.2, False), (0.21, True)])
+def test_near_plane_cull_at_depth_point_two(tz, visible):
+    """The near-plane cull drops a splat whose camera-space depth is at most 0.2 (3DGS convention):
+    identical splats on the axis at t_z = 0.19 and 0.2 leave the view empty, at 0.21 it renders."""
+    cam = axis_camera(33, 33, f=100.0)
+    o, s = 0.7, math.exp(-3.0)
+    sh = np.zeros((16, 3))
+    sh[0] = [0.4, 0.2, 0.1]
+    bg = (0.2, 0.4, 0.6)
+    sc = make_scene([[0, 0, tz]], [[math.log(s)] * 3], [logit(o)], sh_color=[sh], sigma=6.0, bg=bg)
+    r = oracle.render(sc, cam)
+    pr = oracle.project(sc, cam)[0]
+    if visible:
+        assert pr[0] == 1.0 and r["pairs"] > 0
+        c = 0.5 + sh[0] * _zonal(0)
+        assert np.allclose(r["image"][16, 16], (1 - o) * np.array(bg) + o * c, atol=1e-14, rtol=0)
+    else:
+        assert pr[0] == 0.0 and r["pairs"] == 0
+        assert np.all(r["image"] == np.array(bg))
+
+
+def test_splat_beyond_sigma_gets_no_weight_gradient():
+    """Eq. 1 with max(0, 1 - d/sigma): a splat deeper than sigma has w = 0 whatever its weight SH,
+    so its weight SH, and sigma through it, get no gradient.  Beside two splats in front of sigma, the
+    oracle's dL/dsigma equals a central finite difference (the far splat stays clamped under the
+    perturbation) and the far splat's weight-SH gradient is exactly zero."""
+    cam = axis_camera(17, 17, f=100.0)
+    sh = np.zeros((3, 16, 3))
+    sh[0, 0] = [0.5, 0.0, -0.5]
+    sh[1, 0] = [-0.3, 0.6, 0.2]
+    sh[2, 0] = [0.4, -0.4, 0.3]
+    shw = np.zeros((3, 16))
+    shw[0, 0] = 0.4
+    shw[1, 0] = 0.2
+    shw[2, 0] = -0.1
+    sc = make_scene([[0, 0, 7.0], [0.01, 0, 2.0], [-0.02, 0.01, 3.0]], [[-1.0] * 3, [-1.5] * 3, [-1.2] * 3],
+                    [logit(0.6), logit(0.5), logit(0.4)], sh_color=sh, sh_weight=shw, sigma=6.0,
+                    bg=(0.3, 0.2, 0.1))
+    r = oracle.render(sc, cam)
+    g = np.random.default_rng(5).normal(size=r["image"].shape)
+    grads, dsig, _ = oracle.backward(sc, cam, r["sums"], g)
+    assert np.all(grads[0, 59:75] == 0.0)
+    assert np.any(np.abs(grads[1, 59:75]) > 1e-6)
+    h = 1e-6 * sc["sigma"]
+    s0 = sc["sigma"]
+    sc["sigma"] = s0 + h
+    lp = float(np.sum(oracle.render(sc, cam)["image"] * g))
+    sc["sigma"] = s0 - h
+    lm = float(np.sum(oracle.render(sc, cam)["image"] * g))
+    sc["sigma"] = s0
+    fd = (lp - lm) / (2 * h)
+    assert abs(fd) > 1e-6
+    assert abs(fd - dsig) <= 1e-6 * max(1.0, abs(dsig))
