@@ -16,7 +16,13 @@ Tolerances (stated for the FP32 CUDA path against the FP64 oracle):
     weight, 1 - z/sigma) or the near plane within AMB_BAND are excluded (and
     counted).  dL/dsigma (a sum whose terms cancel) is measured against the
     sum of |per-splat terms|, plus its flip allowance.
+    The allowance is capped: per group, the share of kept elements whose
+    error exceeds 1e-4 max|g_ref| without it (they pass only through it) must
+    stay within GRAD_FLIP_MAX, and every comparison prints the raw error,
+    the raw error of the elements whose allowance is zero and those shares.
 """
+import json
+import os
 import numpy as np
 import torch
 
@@ -26,6 +32,9 @@ IMG_TOL = 1e-5
 GRAD_TOL = 1e-4
 AMB_BAND = 3e-4
 AMB_PIX_MAX = 0.01  # cap on the fraction of pixels that pass only through their allowance
+# cap on the share of a group's kept gradient elements that pass only through their allowance:
+# measured at most 0.04 % (0.11 % of splats) at 1M splats / 5 % active, 0 on the smaller cases
+GRAD_FLIP_MAX = 0.002
 
 GROUPS = dict(means=(0, 3), quats=(3, 7), log_scales=(7, 10), opacity_logits=(10, 11), sh_color=(11, 59),
               sh_weight=(59, 75))
@@ -47,10 +56,13 @@ def image_error(img_gpu, ref_img, flip=None):
     scale = max(np.abs(ref_img).max(), 1e-30)
     d = np.abs(a - ref_img).max(axis=2)
     frac = 0.0
+    raw = float(d.max(initial=0.0) / scale)
     if flip is not None:
         frac = float((d > IMG_TOL * scale).mean())
         d = np.maximum(d - flip, 0.0)
-    return float(d.max(initial=0.0) / scale), frac
+    err = float(d.max(initial=0.0) / scale)
+    _record("image", {"err": err, "raw": raw, "flip_pixels": frac})
+    return err, frac
 
 
 def oracle_grads(scene, cam, sums, dL_dC, active=None, window=None):
@@ -58,31 +70,65 @@ def oracle_grads(scene, cam, sums, dL_dC, active=None, window=None):
                                 want_flip=True)
 
 
-def grad_errors(gpu: dict, ref, rows: np.ndarray, keep: np.ndarray, flip=None):
-    """Per group: max over kept rows of (|g_gpu - g_ref| - flip)^+ / max|g_ref|.
+def grad_report(gpu: dict, ref, rows: np.ndarray, keep: np.ndarray, flip=None, tol=GRAD_TOL):
+    """Per group, over the kept rows (all relative to max|g_ref| of the group):
+      err         max of (|g_gpu - g_ref| - flip)^+ (the parity figure),
+      raw         max of |g_gpu - g_ref| (no allowance),
+      raw_noflip  max of |g_gpu - g_ref| over the elements whose allowance is zero,
+      flip_elems  share of elements with |g_gpu - g_ref| > tol max|g_ref| (they pass only through
+                  their allowance), flip_splats the share of rows holding such an element.
     gpu: dict group -> array [len(rows), ...] in the order of `rows`; ref: [N, 75]."""
     out = {}
     for name, (lo, hi) in GROUPS.items():
         g = to_np(gpu[name]).reshape(len(rows), -1)[keep]
         r = ref[rows][keep, lo:hi]
         d = np.abs(g - r)
-        if flip is not None:
-            d = np.maximum(d - flip[rows][keep, lo:hi], 0.0)
         scale = max(np.abs(r).max(initial=0.0), 1e-30)
-        out[name] = float(d.max(initial=0.0) / scale)
+        rep = {"raw": float(d.max(initial=0.0) / scale)}
+        if flip is not None:
+            f = flip[rows][keep, lo:hi]
+            over = d > tol * scale
+            rep["err"] = float(np.maximum(d - f, 0.0).max(initial=0.0) / scale)
+            rep["raw_noflip"] = float(d[f == 0].max(initial=0.0) / scale)
+            rep["flip_elems"] = float(over.mean()) if over.size else 0.0
+            rep["flip_splats"] = float(over.any(axis=1).mean()) if over.size else 0.0
+        else:
+            rep["err"] = rep["raw"]
+        out[name] = rep
     return out
 
 
+def grad_errors(gpu: dict, ref, rows: np.ndarray, keep: np.ndarray, flip=None):
+    """Per group: max over kept rows of (|g_gpu - g_ref| - flip)^+ / max|g_ref|."""
+    return {k: v["err"] for k, v in grad_report(gpu, ref, rows, keep, flip).items()}
+
+
+def _record(kind, rep):
+    """Print one parity record (and append it to $SPARSEOIT_PARITY_LOG when set)."""
+    test = os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0]
+    line = json.dumps({"kind": kind, "test": test, **rep})
+    print("PARITY", line)
+    path = os.environ.get("SPARSEOIT_PARITY_LOG")
+    if path:
+        with open(path, "a") as fh:
+            fh.write(line + "\n")
+
+
 def assert_grads_close(gpu, ref, rows, keep, tol=GRAD_TOL, dsig=None, dsig_ref=None, dsig_scale=None, flip=None,
-                       dsig_flip=0.0):
-    errs = grad_errors(gpu, ref, rows, keep, flip)
-    bad = {k: v for k, v in errs.items() if not v <= tol}
-    assert not bad, f"gradient parity failed: {errs}"
+                       dsig_flip=0.0, flip_max=GRAD_FLIP_MAX):
+    rep = grad_report(gpu, ref, rows, keep, flip, tol)
+    errs = {k: v["err"] for k, v in rep.items()}
     if dsig is not None:
         scale = dsig_scale if dsig_scale is not None else abs(dsig_ref)
+        raw = abs(dsig - dsig_ref) / max(scale, 1e-30)
         rel = max(abs(dsig - dsig_ref) - dsig_flip, 0.0) / max(scale, 1e-30)
         errs["sigma"] = rel
-        assert rel <= tol, f"dsigma {dsig} vs {dsig_ref} (rel {rel:.3g} of {scale:.3g})"
+        rep["sigma"] = {"err": rel, "raw": raw}
+    _record("grad", {"groups": rep})
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, f"gradient parity failed: {errs}"
+    over = {k: v["flip_elems"] for k, v in rep.items() if "flip_elems" in v and not v["flip_elems"] <= flip_max}
+    assert not over, f"too many gradient elements pass only through their allowance: {over}"
     return errs
 
 
