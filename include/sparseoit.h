@@ -142,10 +142,12 @@ typedef struct {
                                       0 = default (4)                          */
     int32_t proj_lanes_per_splat;  /* projection: lanes per splat, 1, 2, 4 or
                                       16; 0 = default (4)                      */
-    int32_t bwd_group_by_cell;     /* backward raster: order each round of a
-                                      tile's splats by the 4x4-pixel cell of
-                                      their centre before assigning warps;
-                                      1 = on, -1 = off, 0 = default (off)      */
+    int32_t bwd_walk;              /* per-splat backward raster: the order in
+                                      which warps take a tile's splats.
+                                      0 = default = 1; 1 = sorted in shared
+                                      memory by the first tile row the
+                                      splat's ellipse reaches (whole-tile
+                                      splats first); 2 = arena order        */
     int32_t raster_tile_order;     /* rasters take tiles heaviest first (tiles
                                       ranked by pair count in four classes per
                                       octave) instead of in index order;
@@ -158,7 +160,12 @@ typedef struct {
                                       tile); 2 = per pixel, warp-reduced
                                       atomics; 3 = per pixel, one atomic set
                                       per contributing pair (3DGS)          */
-    int32_t reserved[1];
+    int32_t raster_persistent;     /* rasters (forward, backward, frozen-sum
+                                      commit) as persistent blocks, as many
+                                      as fit on the device, that take the
+                                      tiles of a call from an atomic queue in
+                                      the raster order; 1 = on, -1 = off,
+                                      0 = default (off)                      */
 } sparseoit_config;
 
 /* Create a context for a scene of max_splats splats and n_views training
@@ -200,7 +207,9 @@ int sparseoit_get_frozen(sparseoit_ctx *ctx, int32_t view, float **d_planes);
  * state that outlives an iteration; this restores them (checkpoint and
  * resume).  planes: 5 planes of H*W floats in the layout of
  * sparseoit_get_frozen, in device or host memory (copied with
- * cudaMemcpyDefault on `stream`; the caller keeps ownership).  The view is
+ * cudaMemcpyDefault on `stream`; the caller keeps ownership, and the planes
+ * must stay valid and unchanged until `stream` has completed the copy --
+ * with pinned host memory the copy is truly asynchronous).  The view is
  * then treated as committed under the current active set: the caller
  * guarantees that the planes are the sums of the complement of that set
  * (for example saved by sparseoit_get_frozen under the same mask) for the
@@ -234,19 +243,34 @@ int sparseoit_backward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const
 
 /* Result of sparseoit_autotune. */
 typedef struct {
-    int32_t fwd_pixels_per_thread;   /* chosen candidate (1, 2 or 4)          */
+    int32_t fwd_pixels_per_thread;   /* chosen forward strip (1, 2 or 4)              */
     int32_t n_candidates;
-    int32_t candidates[4];           /* the candidates tried                  */
-    float ms[4];                     /* mean forward time of each candidate   */
+    int32_t candidates[4];           /* the strips tried                              */
+    float ms[4];                     /* mean forward time of each strip (one block
+                                        per tile)                                     */
+    int32_t fwd_persistent;          /* chosen: 1 = persistent forward raster blocks  */
+    float fwd_persistent_ms;         /* mean forward time, chosen strip, persistent   */
+    int32_t bwd_walk;                /* chosen backward splat order (1 sorted by first
+                                        row, 2 arena order); 0 = not tuned (the
+                                        forward had no targets)                       */
+    int32_t bwd_persistent;          /* chosen: 1 = persistent backward raster blocks */
+    float bwd_ms[4];                 /* mean backward-raster time: sorted, arena,
+                                        sorted persistent, arena persistent            */
 } sparseoit_tuning;
 
-/* Autotuner: times the forward raster's per-thread pixel strip (1x1, 1x2 and
- * 1x4 pixels of the 16x16 tile, i.e. 256 / 128 / 64 threads per tile) on
- * this exact batch -- the arguments are those of sparseoit_forward, which it
- * runs (1 warm-up + `reps` timed calls per candidate, CUDA events on
- * `stream`) -- and keeps the fastest for later calls.  The outputs of the
- * last call are valid forward outputs.  Synchronises `stream`; not for use
- * during stream capture. */
+/* Autotuner over the launch options that matter on a given batch (the tile
+ * stays 16x16: the binning, both rasters and the pixel state are built on
+ * it).  It times, on this exact batch -- the arguments are those of
+ * sparseoit_forward, which it runs -- (1) the forward raster's per-thread
+ * pixel strip (1x1, 1x2 and 1x4 pixels, i.e. 256 / 128 / 64 threads per
+ * tile), then the chosen strip as persistent blocks taking tiles from a
+ * queue; and, when targets are given (fused L1, so the pixel state exists),
+ * (2) the backward raster with the tile's splats sorted by first row or in
+ * arena order, each as one block per tile and as persistent blocks.  Each
+ * candidate: 1 warm-up + `reps` timed runs, CUDA events on `stream`.  The
+ * fastest of each is kept for later calls.  The outputs of the last call are
+ * valid forward outputs (a backward must follow it as after any forward).
+ * Synchronises `stream`; not for use during stream capture. */
 int sparseoit_autotune(sparseoit_ctx *ctx, const sparseoit_splats *splats, const sparseoit_camera *cams,
                        const int32_t *views, int32_t n_views, float *const *d_images, const float *const *d_targets,
                        float *d_loss, int32_t reps, sparseoit_tuning *out, void *stream);
@@ -258,6 +282,18 @@ int sparseoit_reserve_pairs(sparseoit_ctx *ctx, int64_t max_pairs);
  * SPARSEOIT_ERR_CAPACITY if a pair arena overflowed since the last call,
  * SPARSEOIT_ERR_TIMEOUT if a bounded wait gave up, else SPARSEOIT_OK. */
 int sparseoit_status(sparseoit_ctx *ctx, void *stream);
+
+/* Failure injection for tests of the bounded device-side wait (Alg. 2's
+ * binning scan, IdentifyTileRanges, run as a single-pass scan with look-back
+ * over partitions of 1024 tiles): in the next binning of this context
+ * (a forward, a commit or an update), partition `partition` of the tile
+ * scan posts nothing, so every later partition runs out its wait (0.25 s)
+ * and sets the timeout flag; the kernels after the scan then do nothing and
+ * sparseoit_status returns SPARSEOIT_ERR_TIMEOUT.  The outputs of that call
+ * are invalid; the context stays usable and the next call runs normally.
+ * A partition number at or past the last partition has no effect.  The
+ * injection is consumed by the next binning. */
+int sparseoit_inject_scan_stall(sparseoit_ctx *ctx, int32_t partition);
 
 /* Counters of the last forward (synchronises `stream`): number of
  * (splat, tile) pairs binned (M, summed over its views) and the number of
@@ -417,7 +453,9 @@ int sparseoit_scatter_active(sparseoit_ctx *ctx, const sparseoit_rows *active, s
  * caller; each call writes every scratch slot it reads, so no clearing is
  * needed.  The first call on a device looks up the scratch address with
  * cudaGetSymbolAddress for the current device: make it before any stream
- * capture.  Asynchronous on `stream`. */
+ * capture.  That address is kept for the rest of the process, so do not
+ * reset the device (cudaDeviceReset) or destroy its primary context between
+ * calls.  Asynchronous on `stream`. */
 #define SPARSEOIT_STATIC_MAX_SPLATS (16 * 1024 * 1024)
 int sparseoit_compact_active_static(const uint8_t *d_mask, int64_t n, int32_t *d_idx, int64_t *d_count,
                                     void *stream);

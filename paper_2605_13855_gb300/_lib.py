@@ -39,7 +39,7 @@ EXPORTED = (
     "sparseoit_set_profiling", "sparseoit_get_profile", "sparseoit_last_error", "sparseoit_version",
     "sparseoit_compact_active_static", "sparseoit_autotune", "sparseoit_fps_views", "sparseoit_activeness",
     "sparseoit_update_active_set", "sparseoit_adam_step", "sparseoit_loss_l1_dssim", "sparseoit_gather_active",
-    "sparseoit_scatter_active",
+    "sparseoit_scatter_active", "sparseoit_inject_scan_stall",
 )
 STATIC_MAX_SPLATS = 16 * 1024 * 1024
 
@@ -80,14 +80,16 @@ class KernelTime(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("fwd_pixels_per_thread", ctypes.c_int32), ("n_candidates", ctypes.c_int32),
-                ("candidates", ctypes.c_int32 * 4), ("ms", ctypes.c_float * 4)]
+                ("candidates", ctypes.c_int32 * 4), ("ms", ctypes.c_float * 4),
+                ("fwd_persistent", ctypes.c_int32), ("fwd_persistent_ms", ctypes.c_float),
+                ("bwd_walk", ctypes.c_int32), ("bwd_persistent", ctypes.c_int32), ("bwd_ms", ctypes.c_float * 4)]
 
 
 class Config(ctypes.Structure):
     _fields_ = [("max_pairs", ctypes.c_int64), ("fwd_pixels_per_thread", ctypes.c_int32),
-                ("proj_lanes_per_splat", ctypes.c_int32), ("bwd_group_by_cell", ctypes.c_int32),
+                ("proj_lanes_per_splat", ctypes.c_int32), ("bwd_walk", ctypes.c_int32),
                 ("raster_tile_order", ctypes.c_int32), ("bwd_parallel", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("raster_persistent", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -118,6 +120,7 @@ def load(path: str = LIB_PATH):
             "sparseoit_backward": ([vp, P(Splats), P(vp), P(Grads), vp], ctypes.c_int),
             "sparseoit_reserve_pairs": ([vp, i64], ctypes.c_int),
             "sparseoit_status": ([vp, vp], ctypes.c_int),
+            "sparseoit_inject_scan_stall": ([vp, ctypes.c_int32], ctypes.c_int),
             "sparseoit_last_counts": ([vp, vp, P(i64), P(i64)], ctypes.c_int),
             "sparseoit_set_counting": ([vp, i32], ctypes.c_int),
             "sparseoit_set_profiling": ([vp, i32], ctypes.c_int),

@@ -39,7 +39,7 @@ struct sparseoit_ctx {
     int64_t pair_cap = 0;
     int fwd_strip = 4;            // pixels per thread of the forward raster
     int proj_lanes = 4;           // lanes per splat of the projection
-    bool bwd_group = false;       // backward: group a tile's splats by centre cell
+    int bwd_walk = kBwdWalkSorted; // backward raster: pairs sorted by first row, or arena order
     bool tile_order = true;       // rasters take tiles heaviest first
     int bwd_parallel = 1;         // 1 per splat, 2 per pixel warp-reduced, 3 per pixel per-pair atomics
     std::string err;
@@ -68,6 +68,11 @@ struct sparseoit_ctx {
     float4 *d_sgrad = nullptr;
     int64_t sgrad_cap = 0;        // records
     unsigned *d_status = nullptr;
+    void *d_scan = nullptr;        // binning scan scratch (ScanScratch), zeroed before each scan
+    int *d_queue = nullptr;        // tile queues of the persistent rasters (forward, backward)
+    bool fwd_persistent = false;   // forward / sums raster as persistent blocks over a tile queue
+    bool bwd_persistent = false;   // backward raster as persistent blocks over a tile queue
+    int scan_withhold = -1;        // failure injection: the next scan's partition that posts nothing
     int64_t *d_npairs = nullptr;
     unsigned long long *d_contrib = nullptr;
     bool counting = false;
@@ -221,9 +226,13 @@ static int render_pass_bin(sparseoit_ctx *ctx, Batch &b, const sparseoit_splats 
     const int64_t nrec = (int64_t)b.n_views * (n1 + n2);
     if (nrec > 0xffffffffll) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "too many records in one batch");
     b.tile_order = ctx->tile_order ? ctx->d_order : nullptr;
+    b.status = ctx->d_status;
     if (ctx->rec_cap < 3 * nrec || ctx->tile_cap < (int64_t)b.total_tiles + 1)
         return fail(ctx, SPARSEOIT_ERR_STATE, "batch workspace not sized");
-    CK(cudaMemsetAsync(ctx->d_tile_count, 0, (size_t)b.total_tiles * sizeof(int), st), "memset(tile counts)");
+    // the tile counts and the scan scratch after them, zeroed together
+    CK(cudaMemsetAsync(ctx->d_tile_count, 0,
+                       (size_t)((char *)ctx->d_scan - (char *)ctx->d_tile_count) + scan_scratch_bytes(b.total_tiles), st),
+       "memset(tile counts, scan scratch)");
     const SplatPtrs sp = splat_ptrs(s);
     {
         ProfScope ps(ctx, "project", st);
@@ -233,13 +242,16 @@ static int render_pass_bin(sparseoit_ctx *ctx, Batch &b, const sparseoit_splats 
     CK_LAUNCH("project_kernel");
     {
         ProfScope ps(ctx, "scan_tiles", st);
-        launch_scan_tiles(ctx->d_tile_count, b.total_tiles, ctx->d_offsets, ctx->d_cursor, b.tile_order ? ctx->d_order : nullptr,
-                          ctx->pair_cap, ctx->d_status, ctx->d_npairs, st);
+        launch_scan_tiles(ctx->d_tile_count, b.total_tiles, ctx->d_offsets, ctx->d_cursor,
+                          scan_scratch_at(ctx->d_scan, b.total_tiles), ctx->pair_cap, ctx->d_status, ctx->d_npairs,
+                          ctx->scan_withhold, st);
+        ctx->scan_withhold = -1;
     }
     CK_LAUNCH("scan_tiles_kernel");
     {
         ProfScope ps(ctx, "scatter", st);
-        launch_scatter(b, ctx->d_rec, ctx->d_ext, ctx->d_cursor, ctx->d_pairs, ctx->pair_cap, st);
+        launch_scatter(b, ctx->d_rec, ctx->d_ext, ctx->d_cursor, ctx->d_pairs, ctx->pair_cap, ctx->d_tile_count,
+                       scan_scratch_at(ctx->d_scan, b.total_tiles), b.tile_order ? ctx->d_order : nullptr, st);
     }
     CK_LAUNCH("scatter_kernel");
     return SPARSEOIT_OK;
@@ -264,15 +276,47 @@ static int ensure_batch_ws(sparseoit_ctx *ctx, int64_t nrec, int64_t tiles) {
         if (ctx->d_cursor) cudaFree(ctx->d_cursor);
         if (ctx->d_order) cudaFree(ctx->d_order);
         ctx->d_tile_count = ctx->d_offsets = ctx->d_cursor = ctx->d_order = nullptr;
+        ctx->d_scan = nullptr;
         ctx->tile_cap = 0;
         const int64_t n = tiles + 1;
-        CK(cudaMalloc((void **)&ctx->d_tile_count, (size_t)n * sizeof(int)), "cudaMalloc(tile counts)");
+        // the tile counts with the scan scratch after them (256-byte aligned): one memset zeroes both
+        const size_t counts_bytes = ((size_t)n * sizeof(int) + 255) & ~(size_t)255;
+        CK(cudaMalloc((void **)&ctx->d_tile_count, counts_bytes + scan_scratch_bytes(n)), "cudaMalloc(tile counts)");
+        ctx->d_scan = (char *)ctx->d_tile_count + counts_bytes;
         CK(cudaMalloc((void **)&ctx->d_offsets, (size_t)n * sizeof(int)), "cudaMalloc(tile offsets)");
         CK(cudaMalloc((void **)&ctx->d_cursor, (size_t)n * sizeof(int)), "cudaMalloc(tile cursors)");
         CK(cudaMalloc((void **)&ctx->d_order, (size_t)n * sizeof(int)), "cudaMalloc(tile order)");
+        // defined contents from the start (a scan that gave up leaves them as they were)
+        CK(cudaMemset(ctx->d_offsets, 0, (size_t)n * sizeof(int)), "memset(tile offsets)");
+        CK(cudaMemset(ctx->d_cursor, 0, (size_t)n * sizeof(int)), "memset(tile cursors)");
+        CK(cudaMemset(ctx->d_order, 0, (size_t)n * sizeof(int)), "memset(tile order)");
         ctx->tile_cap = n;
     }
     return SPARSEOIT_OK;
+}
+
+// Mean CUDA-event time of `reps` runs of fn (after one warm-up run) on st.
+template <typename F>
+static int time_runs(sparseoit_ctx *ctx, cudaStream_t st, int reps, F fn, float *ms_out) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a), "autotune event");
+    CK(cudaEventCreate(&b), "autotune event");
+    int rc = fn();
+    if (!rc) {
+        cudaEventRecord(a, st);
+        for (int r = 0; r < reps && !rc; ++r) rc = fn();
+        cudaEventRecord(b, st);
+    }
+    float ms = 0.f;
+    if (!rc) {
+        cudaError_t e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e != cudaSuccess) rc = cuda_check(ctx, e, "autotune timing");
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *ms_out = ms / (float)reps;
+    return rc;
 }
 
 extern "C" {
@@ -314,8 +358,15 @@ int sparseoit_create(sparseoit_ctx **out, int64_t max_splats, int32_t n_views, c
         }
         ctx->proj_lanes = l;
     }
-    if (cfg && cfg->bwd_group_by_cell != 0) ctx->bwd_group = cfg->bwd_group_by_cell > 0;
+    if (cfg && cfg->bwd_walk != 0) {
+        if (cfg->bwd_walk != kBwdWalkSorted && cfg->bwd_walk != kBwdWalkArena) {
+            delete ctx;
+            return fail(nullptr, SPARSEOIT_ERR_INVALID_ARG, "bwd_walk must be 0, 1 or 2");
+        }
+        ctx->bwd_walk = cfg->bwd_walk;
+    }
     if (cfg && cfg->raster_tile_order != 0) ctx->tile_order = cfg->raster_tile_order > 0;
+    if (cfg && cfg->raster_persistent != 0) ctx->fwd_persistent = ctx->bwd_persistent = cfg->raster_persistent > 0;
     if (cfg && cfg->bwd_parallel != 0) {
         if (cfg->bwd_parallel < 1 || cfg->bwd_parallel > 3) {
             delete ctx;
@@ -355,6 +406,7 @@ int sparseoit_create(sparseoit_ctx **out, int64_t max_splats, int32_t n_views, c
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_totals, 4 * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->h_totals, 4 * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_pairs, (size_t)ctx->pair_cap * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_queue, 2 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_npairs, sizeof(int64_t));
@@ -373,7 +425,8 @@ int sparseoit_destroy(sparseoit_ctx *ctx) {
     for (float *p : ctx->d_state) if (p) cudaFree(p);
     void *bufs[] = {ctx->d_mask[0], ctx->d_mask[1], ctx->d_idx_active, ctx->d_idx_comp, ctx->d_idx_plus,
                     ctx->d_idx_minus, ctx->d_blk, ctx->d_totals, ctx->d_rec, ctx->d_ext, ctx->d_tile_count,
-                    ctx->d_offsets, ctx->d_cursor, ctx->d_order, ctx->d_pairs, ctx->d_sgrad, ctx->d_status, ctx->d_npairs,
+                    ctx->d_offsets, ctx->d_cursor, ctx->d_order, ctx->d_queue, ctx->d_pairs, ctx->d_sgrad, ctx->d_status,
+                    ctx->d_npairs,
                     ctx->d_contrib, ctx->d_upd_image, ctx->d_upd_loss, ctx->d_ssim_abc, ctx->d_ssim_sums,
                     ctx->d_idx_all};
     for (void *p : bufs) if (p) cudaFree(p);
@@ -477,8 +530,8 @@ int sparseoit_commit_frozen(sparseoit_ctx *ctx, const sparseoit_splats *splats, 
         rc = render_pass_bin(ctx, b, splats, l1, (int)n1, l2, (int)n2, st);
         if (rc) return rc;
         ProfScope ps(ctx, "raster_sums", st);
-        launch_raster_fwd(b, kRasterSums, ctx->fwd_strip, ctx->d_rec, ctx->d_offsets, ctx->d_pairs, ctx->pair_cap, splats->bg, nullptr,
-                          nullptr, st);
+        launch_raster_fwd(b, kRasterSums, ctx->fwd_strip, ctx->d_rec, ctx->d_offsets, ctx->d_pairs, ctx->pair_cap,
+                          splats->bg, nullptr, nullptr, ctx->fwd_persistent ? ctx->d_queue : nullptr, st);
         CK_LAUNCH("raster_fwd_kernel(sums)");
     }
     ctx->view_gen[view] = ctx->generation;
@@ -553,7 +606,7 @@ static int forward_impl(sparseoit_ctx *ctx, const sparseoit_splats *splats, cons
         ProfScope ps(ctx, "raster_fwd", st);
         launch_raster_fwd(b, d_targets ? kRasterFused : kRasterAux, ctx->fwd_strip, ctx->d_rec, ctx->d_offsets, ctx->d_pairs,
                           ctx->pair_cap, splats->bg, d_targets ? d_loss : nullptr,
-                          ctx->counting ? ctx->d_contrib : nullptr, st);
+                          ctx->counting ? ctx->d_contrib : nullptr, ctx->fwd_persistent ? ctx->d_queue : nullptr, st);
     }
     CK_LAUNCH("raster_fwd_kernel");
     ctx->have_fwd = true;
@@ -605,8 +658,8 @@ int sparseoit_backward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const
     {
         ProfScope ps(ctx, "raster_bwd", st);
         if (ctx->bwd_parallel == 1)
-            launch_raster_bwd(b, ctx->bwd_group, ctx->d_rec, ctx->d_offsets, ctx->d_pairs, ctx->pair_cap,
-                              ctx->d_sgrad, st);
+            launch_raster_bwd(b, ctx->bwd_walk, ctx->d_rec, ctx->d_offsets, ctx->d_pairs, ctx->pair_cap,
+                              ctx->d_sgrad, ctx->bwd_persistent ? ctx->d_queue + 1 : nullptr, st);
         else
             launch_raster_bwd_pixel(b, ctx->bwd_parallel == 2, ctx->d_rec, ctx->d_offsets, ctx->d_pairs,
                                     ctx->pair_cap, ctx->d_sgrad, st);
@@ -811,41 +864,65 @@ int sparseoit_autotune(sparseoit_ctx *ctx, const sparseoit_splats *splats, const
     cudaStream_t st = (cudaStream_t)stream;
     const int cand[3] = {1, 2, 4};
     memset(out, 0, sizeof(*out));
-    cudaEvent_t a = nullptr, b = nullptr;
-    CK(cudaEventCreate(&a), "autotune event");
-    CK(cudaEventCreate(&b), "autotune event");
     const bool prof = ctx->profiling;
     ctx->profiling = false;
+    auto fwd = [&]() { return sparseoit_forward(ctx, splats, cams, views, n_views, d_images, d_targets, d_loss, stream); };
+    // (1) the forward strip, one block per tile; then the chosen strip as persistent blocks
+    ctx->fwd_persistent = false;
     int best = ctx->fwd_strip;
     float best_ms = 0.f;
     int rc = SPARSEOIT_OK;
     for (int c = 0; c < 3 && rc == SPARSEOIT_OK; ++c) {
         ctx->fwd_strip = cand[c];
-        rc = sparseoit_forward(ctx, splats, cams, views, n_views, d_images, d_targets, d_loss, stream);
-        if (rc) break;
-        cudaEventRecord(a, st);
-        for (int r = 0; r < reps && rc == SPARSEOIT_OK; ++r)
-            rc = sparseoit_forward(ctx, splats, cams, views, n_views, d_images, d_targets, d_loss, stream);
-        cudaEventRecord(b, st);
-        if (rc) break;
-        cudaError_t e = cudaEventSynchronize(b);
         float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-        if (e != cudaSuccess) { rc = cuda_check(ctx, e, "autotune timing"); break; }
-        ms /= (float)reps;
+        rc = time_runs(ctx, st, reps, fwd, &ms);
+        if (rc) break;
         out->candidates[out->n_candidates] = cand[c];
         out->ms[out->n_candidates] = ms;
         out->n_candidates++;
         if (c == 0 || ms < best_ms) { best_ms = ms; best = cand[c]; }
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    ctx->profiling = prof;
     ctx->fwd_strip = best;
     out->fwd_pixels_per_thread = best;
+    if (!rc) {
+        ctx->fwd_persistent = true;
+        rc = time_runs(ctx, st, reps, fwd, &out->fwd_persistent_ms);
+        ctx->fwd_persistent = !rc && out->fwd_persistent_ms < best_ms;
+        out->fwd_persistent = ctx->fwd_persistent ? 1 : 0;
+    }
+    // (2) the backward raster on the fused forward's pixel state
+    if (!rc && d_targets) rc = fwd();
+    if (!rc && d_targets) {
+        Batch &b = ctx->last_batch;
+        const int64_t nrec = (int64_t)b.n_views * ctx->last_n_list;
+        CK(grow(&ctx->d_sgrad, &ctx->sgrad_cap, 3 * nrec), "cudaMalloc(screen grads)");
+        const int walks[2] = {kBwdWalkSorted, kBwdWalkArena};
+        float best_b = 0.f;
+        for (int k = 0; k < 4 && !rc; ++k) {
+            const int walk = walks[k & 1];
+            const bool pers = k >= 2;
+            auto bwd = [&]() {
+                CK(cudaMemsetAsync(ctx->d_sgrad, 0, (size_t)(3 * nrec) * sizeof(float4), st), "memset(screen grads)");
+                launch_raster_bwd(b, walk, ctx->d_rec, ctx->d_offsets, ctx->d_pairs, ctx->pair_cap, ctx->d_sgrad,
+                                  pers ? ctx->d_queue + 1 : nullptr, st);
+                return cuda_check(ctx, cudaGetLastError(), "raster_bwd_kernel");
+            };
+            rc = time_runs(ctx, st, reps, bwd, &out->bwd_ms[k]);
+            if (!rc && (k == 0 || out->bwd_ms[k] < best_b)) {
+                best_b = out->bwd_ms[k];
+                out->bwd_walk = walk;
+                out->bwd_persistent = pers ? 1 : 0;
+            }
+        }
+        if (!rc) {
+            ctx->bwd_walk = out->bwd_walk;
+            ctx->bwd_persistent = out->bwd_persistent != 0;
+        }
+    }
+    ctx->profiling = prof;
     if (rc) return rc;
     // leave valid outputs of the chosen configuration
-    return sparseoit_forward(ctx, splats, cams, views, n_views, d_images, d_targets, d_loss, stream);
+    return fwd();
 }
 
 int sparseoit_reserve_pairs(sparseoit_ctx *ctx, int64_t max_pairs) {
@@ -859,6 +936,13 @@ int sparseoit_reserve_pairs(sparseoit_ctx *ctx, int64_t max_pairs) {
     CK(cudaMalloc((void **)&ctx->d_pairs, (size_t)max_pairs * sizeof(uint32_t)), "cudaMalloc(pairs)");
     ctx->pair_cap = max_pairs;
     ctx->have_fwd = false;
+    return SPARSEOIT_OK;
+}
+
+int sparseoit_inject_scan_stall(sparseoit_ctx *ctx, int32_t partition) {
+    if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
+    if (partition < 0) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "partition must be >= 0");
+    ctx->scan_withhold = partition;
     return SPARSEOIT_OK;
 }
 

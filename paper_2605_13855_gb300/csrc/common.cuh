@@ -64,8 +64,41 @@ struct Batch {
     int n_list;                   // list entries (records) per view
     int pad_;
     const int *tile_order;        // raster block -> global tile (heaviest first); null = identity
+    const unsigned *status;       // device status word (kStatusTimeout: the binning scan gave up)
     ViewDesc v[kMaxViews];
 };
+
+// The tile scan of this batch's binning gave up (a bounded wait ran out): its
+// offsets and tile order are incomplete, so the kernels after it do nothing.
+// (Read through the read-only cache: no kernel after the scan writes the
+// word, and the one line is then fetched once per SM instead of once per warp.)
+__device__ __forceinline__ bool bin_failed(const Batch &b) {
+    return b.status && (__ldg(b.status) & kStatusTimeout);
+}
+
+// Binning scan (project.cu): partitions of kScanItems tiles, one block of
+// kScanThreads threads each; per-batch scratch (zeroed before every scan).
+constexpr int kScanThreads = 256, kScanPer = 4, kScanItems = kScanThreads * kScanPer;
+constexpr int kLoadClasses = 128;  // raster tile-order classes (four per octave of pair count)
+struct ScanScratch {
+    unsigned long long *state;    // [partitions] posted aggregate / inclusive prefix
+    int *ticket;                  // next partition number
+    int *class_hist;              // [kLoadClasses] tiles per load class
+    int *class_cursor;            // [kLoadClasses] placement counters of the tile order
+};
+inline int scan_partitions(int total) { return total > 0 ? (total + kScanItems - 1) / kScanItems : 1; }
+// Bytes of the scratch for `tiles` tiles, and its layout in one allocation.
+inline size_t scan_scratch_bytes(int64_t tiles) {
+    return (size_t)scan_partitions((int)tiles) * 8 + (2 + 2 * kLoadClasses) * sizeof(int);
+}
+inline ScanScratch scan_scratch_at(void *p, int64_t tiles) {
+    ScanScratch s;
+    s.state = reinterpret_cast<unsigned long long *>(p);
+    s.ticket = reinterpret_cast<int *>(s.state + scan_partitions((int)tiles));
+    s.class_hist = s.ticket + 2;
+    s.class_cursor = s.class_hist + kLoadClasses;
+    return s;
+}
 
 // Global tile a raster block works on: blocks are handed out heaviest tile
 // first, so that the long tiles start early instead of forming the tail.

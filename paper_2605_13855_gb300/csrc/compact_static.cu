@@ -20,7 +20,9 @@
 //     wrong results: serialise them.
 //   * The first call on a device looks up the array's device address with
 //     cudaGetSymbolAddress (with that device current) and caches it; make that
-//     first call before any stream capture on that device.
+//     first call before any stream capture on that device.  The cached address
+//     is kept for the process: a device reset (cudaDeviceReset) or a new
+//     primary context between calls would leave it stale.
 #include <cuda_runtime.h>
 
 #include <mutex>

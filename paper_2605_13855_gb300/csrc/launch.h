@@ -7,22 +7,28 @@ namespace soit {
 // lanes = lanes per splat of the projection (4 or 16).
 int launch_project(const Batch &b, const SplatPtrs &sp, bool bf16, int lanes, const int *list1, int n1,
                    const int *list2, int n2, float4 *rec, float4 *ext, int *tile_count, cudaStream_t st);
-// order (nullable): receives the raster blocks' tile order, heaviest load class first.
-int launch_scan_tiles(const int *count, int total, int *offsets, int *cursor, int *order, int64_t cap,
-                      unsigned *status, int64_t *pairs_out, cudaStream_t st);
+// sc: the zeroed scan scratch; withhold: partition that posts nothing (failure injection), else -1.
+int launch_scan_tiles(const int *count, int total, int *offsets, int *cursor, ScanScratch sc, int64_t cap,
+                      unsigned *status, int64_t *pairs_out, int withhold, cudaStream_t st);
+// order (nullable): receives the raster blocks' tile order, heaviest load class first (placed by the
+// scatter's first blocks from the scan's class histogram).
 int launch_scatter(const Batch &b, const float4 *rec, const float4 *ext, int *cursor, uint32_t *pairs, int64_t cap,
-                   cudaStream_t st);
+                   const int *count, ScanScratch sc, int *order, cudaStream_t st);
 
 enum RasterMode { kRasterFused = 0, kRasterAux = 1, kRasterSums = 2 };
 // strip = pixels per thread of the forward raster (1, 2 or 4).
+// queue (nullable): a zeroed-at-launch counter; given, the raster runs persistent blocks (as many as
+// fit on the device) that take tiles from it in the raster order, else one block per tile.
 int launch_raster_fwd(const Batch &b, int mode, int strip, const float4 *rec, const int *offsets,
                       const uint32_t *pairs, int64_t cap, const float bg[3], float *loss, unsigned long long *contrib,
-                      cudaStream_t st);
+                      int *queue, cudaStream_t st);
 
 int launch_prep_state(const Batch &b, const float bg[3], cudaStream_t st);
-// group: order each round of a tile's splats by centre cell before splitting it into warps.
-int launch_raster_bwd(const Batch &b, bool group, const float4 *rec, const int *offsets, const uint32_t *pairs,
-                      int64_t cap, float4 *sgrad, cudaStream_t st);
+// walk: kBwdWalkSorted (each tile's pairs sorted by first row before the warps take them) or
+// kBwdWalkArena (arena order).
+enum BwdWalk { kBwdWalkSorted = 1, kBwdWalkArena = 2 };
+int launch_raster_bwd(const Batch &b, int walk, const float4 *rec, const int *offsets, const uint32_t *pairs,
+                      int64_t cap, float4 *sgrad, int *queue, cudaStream_t st);
 
 // Per-pixel backward (raster_bwd_pixel.cu), the ablation baseline: warp_reduce = sum the warp's
 // pixels before the atomics, else one set of atomics per contributing pair.

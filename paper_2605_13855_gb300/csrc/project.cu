@@ -178,12 +178,8 @@ __global__ void __launch_bounds__(256, 3) project_kernel(const __grid_constant__
     }
 }
 
-// Exclusive scan of the tile counts of the batch by one block of 1024
-// threads, 8 consecutive counts per thread per chunk.  offsets[total] = M.
-// cursor[t] = offsets[t] for the scatter.  Flags kStatusCapacity if M > cap.
 // Load class of a tile with c pairs: 0 for an empty tile, else 1 + 4 e + m
 // for c = 2^e (1 + m/4 + ...), i.e. four classes per octave (<= 124).
-constexpr int kLoadClasses = 128;
 __device__ __forceinline__ int load_class(int c) {
     if (c <= 0) return 0;
     const int e = 31 - __clz(c);
@@ -191,89 +187,137 @@ __device__ __forceinline__ int load_class(int c) {
     return 1 + 4 * e + m;
 }
 
-// One block: exclusive scan of the per-tile pair counts into offsets (and
-// the scatter cursors), the capacity check, and, when order is given, the
-// order in which the raster blocks take the tiles: by load class, heaviest
-// first (a bucketed longest-processing-time-first schedule; the order
-// within a class is arbitrary and changes no result).
-__global__ void __launch_bounds__(1024) scan_tiles_kernel(const int *__restrict__ count, int total,
-                                                          int *__restrict__ offsets, int *__restrict__ cursor,
-                                                          int *__restrict__ order, int64_t cap, unsigned *status,
-                                                          int64_t *pairs_out) {
-    // one chunk of 8192 counts at a time, staged through shared memory so that the global loads
-    // and stores are coalesced; element e sits at e + e / 32 (thread t's eight consecutive elements
-    // then fall in distinct banks across the warp)
-    __shared__ int sv[8192 + 8192 / 32];
-    __shared__ int warp_sums[32];
-    __shared__ int carry_s;
-    __shared__ int cls_pos[kLoadClasses];
+// %globaltimer (nanoseconds) for the deadline of a bounded wait.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Partition state words of the look-back scan: flag in the top two bits, value below.
+constexpr unsigned long long kPartAgg = 1ull << 62, kPartPrefix = 2ull << 62, kPartValue = (1ull << 62) - 1;
+constexpr unsigned long long kScanWaitNs = 250000000ull;  // a partition gives up waiting after 0.25 s
+
+// Exclusive scan of the batch's per-tile pair counts into offsets (and the
+// scatter cursors) in one pass over kScanItems-tile partitions, by decoupled
+// look-back: a block takes the next partition number from a ticket counter
+// (so that every lower partition belongs to a block that is already running),
+// scans its counts, posts its aggregate, then walks back over the lower
+// partitions' posts until it meets an inclusive prefix, and posts its own.
+// Each wait for a post is bounded: after kScanWaitNs the block sets
+// kStatusTimeout, writes nothing and returns (the kernels after it see the
+// status word and skip their work).  The last partition writes offsets[total]
+// = M and flags kStatusCapacity if M exceeds the pair arena.  Each block also
+// adds its tiles' load classes into the batch's class histogram.
+// `withhold`: the partition that posts nothing (failure injection for tests;
+// -1 in normal use).
+__global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const int *__restrict__ count, int total,
+                                                                  int *__restrict__ offsets,
+                                                                  int *__restrict__ cursor, ScanScratch sc,
+                                                                  int64_t cap, unsigned *status, int64_t *pairs_out,
+                                                                  int withhold) {
+    __shared__ int part_s, warp_sums[kScanThreads / 32];
+    __shared__ long long excl_s;
+    __shared__ int bad_s;
+    __shared__ int cls[kLoadClasses];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) carry_s = 0;
+    if (tid == 0) part_s = atomicAdd(sc.ticket, 1);
+    for (int k = tid; k < kLoadClasses; k += kScanThreads) cls[k] = 0;
     __syncthreads();
-    for (int base = 0; base < total; base += 1024 * 8) {
-        const int nb = min(1024 * 8, total - base);
-        for (int i = tid; i < 1024 * 8; i += 1024) sv[i + (i >> 5)] = i < nb ? count[base + i] : 0;
-        __syncthreads();
-        int vals[8];
-        int local = 0;
+    const int part = part_s;
+    const int base = part * kScanItems + tid * kScanPer;
+    int v[kScanPer], local = 0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int e = tid * 8 + k;
-            vals[k] = sv[e + (e >> 5)];
-            local += vals[k];
-        }
-        int incl = local;
+    for (int k = 0; k < kScanPer; ++k) {
+        v[k] = base + k < total ? count[base + k] : 0;
+        local += v[k];
+        if (base + k < total) atomicAdd(&cls[load_class(v[k])], 1);
+    }
+    int incl = local;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int ws = lane < kScanThreads / 32 ? warp_sums[lane] : 0;
+        int wi = ws;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += y;
+            const int y = __shfl_up_sync(0xffffffffu, wi, off);
+            if (lane >= off) wi += y;
         }
-        if (lane == 31) warp_sums[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            int ws = warp_sums[lane];
-            int wi = ws;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, wi, off);
-                if (lane >= off) wi += y;
+        if (lane < kScanThreads / 32) warp_sums[lane] = wi - ws;  // exclusive
+        if (lane == kScanThreads / 32 - 1) {                      // this thread holds the aggregate
+            const unsigned long long agg = (unsigned long long)wi;
+            unsigned long long *state = sc.state;
+            long long excl = 0;
+            int bad = 0;
+            if (part != withhold) atomicExch(state + part, (part == 0 ? kPartPrefix : kPartAgg) | agg);
+            if (part > 0) {
+                const uint64_t deadline = global_ns() + kScanWaitNs;
+                for (int j = part - 1; j >= 0;) {
+                    const unsigned long long w = *(volatile unsigned long long *)(state + j);
+                    if ((w & ~kPartValue) == 0) {  // not posted yet
+                        if (global_ns() > deadline) {
+                            bad = 1;
+                            break;
+                        }
+                        __nanosleep(64);
+                        continue;
+                    }
+                    excl += (long long)(w & kPartValue);
+                    if (w & kPartPrefix) break;
+                    --j;
+                }
+                if (!bad && part != withhold)
+                    atomicExch(state + part, kPartPrefix | (unsigned long long)(excl + (long long)agg));
             }
-            warp_sums[lane] = wi - ws;  // exclusive
+            if (bad) atomicOr(status, kStatusTimeout);
+            excl_s = excl;
+            bad_s = bad;
+            if (!bad && (int64_t)(part + 1) * kScanItems >= total) {  // the last partition
+                const long long M = excl + (long long)agg;
+                offsets[total] = (int)M;
+                if (pairs_out) *pairs_out = M;
+                if (M > cap) atomicOr(status, kStatusCapacity);
+            }
         }
-        __syncthreads();
-        const int carry = carry_s;
-        int run = carry + warp_sums[warp] + incl - local;
+    }
+    __syncthreads();
+    if (bad_s) return;
+    int run = (int)excl_s + warp_sums[warp] + incl - local;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int e = tid * 8 + k;
-            sv[e + (e >> 5)] = run;
-            run += vals[k];
+    for (int k = 0; k < kScanPer; ++k) {
+        if (base + k < total) {
+            offsets[base + k] = run;
+            cursor[base + k] = run;
         }
-        __syncthreads();
-        for (int i = tid; i < nb; i += 1024) {
-            const int o = sv[i + (i >> 5)];
-            offsets[base + i] = o;
-            cursor[base + i] = o;
-        }
-        if (tid == 1023) carry_s = run;
-        __syncthreads();
+        run += v[k];
     }
-    if (tid == 0) {
-        offsets[total] = carry_s;
-        if (pairs_out) *pairs_out = carry_s;
-        if ((int64_t)carry_s > cap) atomicOr(status, kStatusCapacity);
-    }
-    if (!order) return;
-    for (int k = tid; k < kLoadClasses; k += 1024) cls_pos[k] = 0;
-    __syncthreads();
-    for (int i = tid; i < total; i += 1024) atomicAdd(&cls_pos[load_class(count[i])], 1);
-    __syncthreads();
-    if (warp == 0) {  // first position of each class, heaviest class first: a warp scan over
-                      // the classes in descending order, four per lane
+    for (int k = tid; k < kLoadClasses; k += kScanThreads)
+        if (cls[k]) atomicAdd(sc.class_hist + k, cls[k]);
+}
+
+// The raster blocks' tile order: by load class, heaviest first (a bucketed
+// longest-processing-time-first schedule; the order within a class is
+// arbitrary and changes no result).  Block `blk` places tiles
+// [256 blk, 256 blk + 256): it derives the classes' first positions from the
+// batch's class histogram, reserves one range per class for its tiles with
+// one atomic, and places them.  Run by the first blocks of the scatter (the
+// scan is complete by then).
+__device__ __forceinline__ void place_tile_order(const int *__restrict__ count, int total, const ScanScratch &sc,
+                                                 int *__restrict__ order, int blk) {
+    __shared__ int first[kLoadClasses], local[kLoadClasses], base_s[kLoadClasses];
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int k = tid; k < kLoadClasses; k += kScanThreads) local[k] = 0;
+    if (tid < 32) {  // descending exclusive scan of the class histogram, four classes per lane
         int h[4], sum = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            h[j] = cls_pos[kLoadClasses - 1 - (4 * lane + j)];
+            h[j] = sc.class_hist[kLoadClasses - 1 - (4 * lane + j)];
             sum += h[j];
         }
         int incl = sum;
@@ -285,12 +329,22 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(const int *__restrict_
         int run = incl - sum;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            cls_pos[kLoadClasses - 1 - (4 * lane + j)] = run;
+            first[kLoadClasses - 1 - (4 * lane + j)] = run;
             run += h[j];
         }
     }
     __syncthreads();
-    for (int i = tid; i < total; i += 1024) order[atomicAdd(&cls_pos[load_class(count[i])], 1)] = i;
+    const int t = blk * kScanThreads + tid;
+    int c = 0, slot = 0;
+    if (t < total) {
+        c = load_class(count[t]);
+        slot = atomicAdd(&local[c], 1);
+    }
+    __syncthreads();
+    for (int k = tid; k < kLoadClasses; k += kScanThreads)
+        if (local[k]) base_s[k] = first[k] + atomicAdd(sc.class_cursor + k, local[k]);
+    __syncthreads();
+    if (t < total) order[base_s[c] + slot] = t;
 }
 
 // One warp per list entry.  Lanes compute the column range of one tile row
@@ -298,21 +352,28 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(const int *__restrict_
 // entry's tile list, and each lane then takes one (row, column) of it, so a
 // typical splat costs one round of position-returning atomics instead of one
 // per row.
+// The first order_blocks blocks (256 threads) also place the raster tile order (place_tile_order).
 __global__ void __launch_bounds__(256, 8) scatter_kernel(const __grid_constant__ Batch b,
                                                          const float4 *__restrict__ rec,
                                                          const float4 *__restrict__ ext, int *__restrict__ cursor,
-                                                         uint32_t *__restrict__ pairs, int64_t cap) {
+                                                         uint32_t *__restrict__ pairs, int64_t cap,
+                                                         const int *__restrict__ count, ScanScratch sc, int *order,
+                                                         int order_blocks) {
+    if ((int)blockIdx.x < order_blocks && !bin_failed(b)) place_tile_order(count, b.total_tiles, sc, order, blockIdx.x);
     const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= b.n_list) return;  // whole warps leave together
     for (int v = 0; v < b.n_views; ++v) {
         const ViewDesc &vd = b.v[v];
         const int64_t qidx = (int64_t)v * b.n_list + r;
-        // the three loads are issued together (the record is read even when the splat is culled)
+        // the loads are issued together (the record is read even when the splat is culled), the
+        // status word with them: if the tile scan gave up, its offsets are incomplete
         const float4 e = ext[qidx];
         const float4 r0 = rec[3 * qidx + 0];
         const float B2 = rec[3 * qidx + 1].x;
+        const unsigned stat = __ldg(b.status);
         int ty0, ty1;
+        if (stat & kStatusTimeout) return;
         if (!(e.x > 0.f)) continue;
         if (!tile_rows(vd, r0.y, e, ty0, ty1)) continue;
         for (int tyb = ty0; tyb <= ty1; tyb += 32) {
@@ -377,16 +438,20 @@ int launch_project(const Batch &b, const SplatPtrs &sp, bool bf16, int lanes, co
     return 0;
 }
 
-int launch_scan_tiles(const int *count, int total, int *offsets, int *cursor, int *order, int64_t cap,
-                      unsigned *status, int64_t *pairs_out, cudaStream_t st) {
-    scan_tiles_kernel<<<1, 1024, 0, st>>>(count, total, offsets, cursor, order, cap, status, pairs_out);
+int launch_scan_tiles(const int *count, int total, int *offsets, int *cursor, ScanScratch sc, int64_t cap,
+                      unsigned *status, int64_t *pairs_out, int withhold, cudaStream_t st) {
+    scan_tiles_kernel<<<scan_partitions(total), kScanThreads, 0, st>>>(count, total, offsets, cursor, sc, cap, status,
+                                                                       pairs_out, withhold);
     return 0;
 }
 
 int launch_scatter(const Batch &b, const float4 *rec, const float4 *ext, int *cursor, uint32_t *pairs, int64_t cap,
-                   cudaStream_t st) {
-    if (b.n_list == 0) return 0;
-    scatter_kernel<<<(int)(((int64_t)b.n_list * 32 + 255) / 256), 256, 0, st>>>(b, rec, ext, cursor, pairs, cap);
+                   const int *count, ScanScratch sc, int *order, cudaStream_t st) {
+    const int order_blocks = order ? (b.total_tiles + kScanThreads - 1) / kScanThreads : 0;
+    const int scatter_blocks = (int)(((int64_t)b.n_list * 32 + 255) / 256);
+    const int grid = scatter_blocks > order_blocks ? scatter_blocks : order_blocks;
+    if (grid == 0) return 0;
+    scatter_kernel<<<grid, 256, 0, st>>>(b, rec, ext, cursor, pairs, cap, count, sc, order, order_blocks);
     return 0;
 }
 

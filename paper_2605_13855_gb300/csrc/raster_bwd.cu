@@ -2,19 +2,33 @@
 //
 // Per-splat parallel: a tile's 256 pixel states are loaded into shared
 // memory once; each warp takes 32 of the tile's splats (lane = splat) and
-// walks the tile's pixels, reading each pixel's state as a shared-memory
-// broadcast.  Nothing is stored per pixel in the forward except the state,
-// the per-pair alpha is recomputed from the same record, and each lane ends
-// the tile with its splat's full tile gradient in registers, added with one
+// walks the tile's rows, each lane evaluating its own splat at the pixels of
+// the row.  Nothing is stored per pixel in the forward except the state, the
+// per-pair alpha is recomputed from the same record, and each lane ends the
+// tile with its splat's full tile gradient in registers, added with one
 // vector atomic per 4 fields.  No pair is evaluated twice.
 //
-// Per pixel state (g = dL/dC), five planes: B g (3), A = T g.(F - c0) and
+// Per pixel state (g = dL/dC), five values: B g (3), A = T g.(F - c0) and
 // -B g.F, with B = (1 - T)/Q (0 if Q = 0).  Eq. 10 contracted with g gives,
 // per pair, with D = B (g.c - g.F) = (B g).c + (-B g.F),
 //   dL/da = A/(1 - a) + w D,  dL/dw = a D,  dL/dc = w a (B g),
 // and, unless a is clamped at 0.99, dL/d(ln o) = a dL/da and
-// dL/ds = -ln2 a dL/da, chained to (mu'x, mu'y, r, A2, B2) below.  Each warp
-// walks only the tile rows that some lane's ellipse reaches.
+// dL/ds = -ln2 a dL/da, chained to (mu'x, mu'y, r, A2, B2) below.
+//
+// The warps take groups of 32 of the tile's splats and walk the rows their
+// lanes' ellipses reach, eight pixels per warp vote (a group of four steps
+// runs when some lane has a contributing pixel in it; every lane evaluates
+// the same pixels, so the state loads are broadcasts).  By default each chunk
+// of up to 1024 of the tile's pairs is first counting-sorted in shared memory
+// by where the splat starts in the tile (splats whose cutoff ellipse contains
+// the whole tile first, then by first row), and the warps take consecutive
+// groups from a shared counter, so that a warp's lanes reach similar rows;
+// the launch option bwd_walk = 2 takes the pairs in arena order instead.
+// Each lane evaluates two adjacent columns per step with paired FP32
+// instructions (f32x2 FMA / multiply / add, one issue slot for two values);
+// components of the paired operations round exactly like their scalar
+// counterparts, so contribution decisions stay identical to the forward
+// raster's.
 #include "common.cuh"
 #include "launch.h"
 #include "pair_eval.cuh"
@@ -30,21 +44,6 @@ namespace soit {
 // (the dy sums taken per tile row, where dy is constant) gives
 //   dL/dmu'x = -K A2 Se,  dL/dmu'y = K (A2 r Se - B2^2 Sdy),
 //   dL/dr = -K A2 Sey,    dL/dA2 = K See / A2,  dL/dB2 = K B2 Sdyy.
-// kGroup: before a round of the tile's splats (one per thread) is split into warps, a
-// shared-memory counting sort puts first the splats whose cutoff ellipse
-// contains the whole tile, then the others by the 4x4-pixel cell of the tile
-// that holds their centre (clamped).  A warp whose splats all contain the
-// tile evaluates every pixel without the cutoff test (no divergence); the
-// others tend to share rows and columns.
-//
-// Each lane evaluates two adjacent columns per step with paired FP32
-// instructions (f32x2 FMA / multiply / add, one issue slot for two values);
-// the pixel states sit in shared memory as planes, so that one 128-bit
-// broadcast load fetches a component for two steps.
-// Components of the paired operations round exactly like their scalar
-// counterparts, so contribution decisions stay identical to the forward
-// raster's.
-constexpr int kBwdKeys = 18;  // splat classes of the optional per-round ordering
 
 // Per-lane accumulators of one splat over the tile (see the sums above).
 struct BwdAcc {
@@ -52,29 +51,60 @@ struct BwdAcc {
     float Se, Sey, Sd, Sdy, Sdyy;
 };
 struct BwdSplat {
-    float2 A2p, wp, l2op, c0p, c1p, c2p;
-    float A2dx0, dy0, rA2, B2, thr;
+    float2 A2p, wp, c0p, c1p, c2p;
+    float A2dx0, dy0, rA2, B2, log2o;
 };
 
-// Pixel state of the tile: five planes (B g0, B g1, B g2, A, -B g.F), four
-// adjacent pixels of a row per float4, so that five broadcast loads fetch
-// the state of two steps.
-struct BwdState {
+// The state of two adjacent pixels (x, x + 1) of a row: B g (3 components), A
+// and -B g.F, each as an f32x2 pair in column order.
+struct PixPair {
+    float2 b0, b1, b2, A, nbF;
+};
+
+// The tile's pixel state: five planes (B g0, B g1, B g2, A, -B g.F) of the
+// 256 pixels, four adjacent pixels of a row per float4, so that five
+// broadcast loads fetch the state of two steps.
+struct TileState {
     float4 p[5][kTilePix / 4];
+    // pixel pairs (2m, 2m + 1) and (2m + 2, 2m + 3) of row ky, m even
+    __device__ __forceinline__ void get2(int ky, int m, PixPair &lo, PixPair &hi) const {
+        const int kq = ky * (kTile / 4) + (m >> 1);
+        const float4 u0 = p[0][kq], u1 = p[1][kq], u2 = p[2][kq], u3 = p[3][kq], u4 = p[4][kq];
+        lo = {make_float2(u0.x, u0.y), make_float2(u1.x, u1.y), make_float2(u2.x, u2.y), make_float2(u3.x, u3.y),
+              make_float2(u4.x, u4.y)};
+        hi = {make_float2(u0.z, u0.w), make_float2(u1.z, u1.w), make_float2(u2.z, u2.w), make_float2(u3.z, u3.w),
+              make_float2(u4.z, u4.w)};
+    }
 };
 
-// One step of a lane: pixels (2k, 2k + 1) of a row against the lane's splat,
+// The tile's pixel state from the view's five planes into shared memory (zero
+// outside the view).
+template <int kThreads>
+__device__ __forceinline__ void load_tile_state(const ViewDesc &vd, int tx, int ty, TileState &S) {
+#pragma unroll
+    for (int t = threadIdx.x; t < kTilePix; t += kThreads) {
+        const int x = tx * kTile + (t & (kTile - 1)), y = ty * kTile + (t >> 4);
+        float st5[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        if (x < vd.W && y < vd.H) {
+            const int64_t HW = (int64_t)vd.W * vd.H, pix = (int64_t)y * vd.W + x;
+            const float *st = vd.state;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) st5[k] = st[k * HW + pix];
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) reinterpret_cast<float *>(S.p[k])[t] = st5[k];
+    }
+}
+
+// One step of a lane: pixels (2m, 2m + 1) of a row against the lane's splat,
 // given their exponents and cutoff decisions; lanes without a contributing
 // pixel run it with a = 0, which adds exact zeros.  kClamp: some lane's splat
 // can reach the 0.99 clamp; without it min(a, 0.99) = a and the clamp
 // selects are left out (same results).
 template <bool kClamp>
-__device__ __forceinline__ void bwd_step(const BwdSplat &bs, float2 e1, float2 sq, bool in0, bool in1, float2 b0,
-                                         float2 b1, float2 b2, float2 Ap, float2 nbF, float2 &Rd, float2 &Re,
-                                         BwdAcc &acc) {
+__device__ __forceinline__ void bwd_step(const BwdSplat &bs, float2 e1, float2 lg, bool in0, bool in1,
+                                         const PixPair &ps, float2 &Rd, float2 &Re, BwdAcc &acc) {
     const float2 m1 = make_float2(-1.f, -1.f), one2 = make_float2(1.f, 1.f);
-    // log2 o - s: -s + log2 o rounds once, exactly like the forward's subtraction
-    const float2 lg = __ffma2_rn(sq, m1, bs.l2op);
     const float ar0 = fast_exp2(lg.x), ar1 = fast_exp2(lg.y);
     float2 a, am;
     if (kClamp) {
@@ -85,14 +115,14 @@ __device__ __forceinline__ void bwd_step(const BwdSplat &bs, float2 e1, float2 s
         a = make_float2(in0 ? ar0 : 0.f, in1 ? ar1 : 0.f);
         am = a;
     }
-    const float2 D = __ffma2_rn(b0, bs.c0p, __ffma2_rn(b1, bs.c1p, __ffma2_rn(b2, bs.c2p, nbF)));
+    const float2 D = __ffma2_rn(ps.b0, bs.c0p, __ffma2_rn(ps.b1, bs.c1p, __ffma2_rn(ps.b2, bs.c2p, ps.nbF)));
     const float2 oma = __ffma2_rn(a, m1, one2);  // 1 - a
     const float2 inv = make_float2(fast_rcp(oma.x), fast_rcp(oma.y));
-    const float2 dLda = __ffma2_rn(Ap, inv, __fmul2_rn(bs.wp, D));
+    const float2 dLda = __ffma2_rn(ps.A, inv, __fmul2_rn(bs.wp, D));
     acc.gw = __ffma2_rn(a, D, acc.gw);
-    acc.gc0 = __ffma2_rn(a, b0, acc.gc0);  // times w in the epilogue
-    acc.gc1 = __ffma2_rn(a, b1, acc.gc1);
-    acc.gc2 = __ffma2_rn(a, b2, acc.gc2);
+    acc.gc0 = __ffma2_rn(a, ps.b0, acc.gc0);  // times w in the epilogue
+    acc.gc1 = __ffma2_rn(a, ps.b1, acc.gc1);
+    acc.gc2 = __ffma2_rn(a, ps.b2, acc.gc2);
     const float2 da = __fmul2_rn(dLda, am);
     Rd = __fadd2_rn(Rd, da);
     const float2 qd = __fmul2_rn(da, e1);
@@ -100,46 +130,41 @@ __device__ __forceinline__ void bwd_step(const BwdSplat &bs, float2 e1, float2 s
     acc.See = __ffma2_rn(qd, e1, acc.See);
 }
 
-// Rows [rlo, rhi] of the tile for one lane's splat.  kTest: test every pixel
-// against the cutoff (the pair contributes iff s <= thr); without it every
-// pixel of the rows contributes (the caller knows the whole tile lies inside
-// the cutoff ellipse).  A row is taken kQuads groups of four pixels at a
-// time: the group's two or four steps run when some lane of the warp has a
+// Rows [rlo, rhi] of the tile.  kTest: test every pixel against the cutoff
+// (the pair contributes iff its exponent reaches -log2 255); without it every
+// pixel contributes (the warp's splats all contain the whole tile, or are
+// empty records whose alpha is 0).  A row is taken eight pixels at a time:
+// the four steps of a group run when some lane of the warp has a
 // contributing pixel in it (a warp vote, so the branch is uniform), and run
 // without branches between them, so that their chains interleave.
-template <bool kTest, bool kClamp, int kQuads>
-__device__ __forceinline__ void bwd_rows(const BwdSplat &bs, const BwdState &S, int rlo, int rhi, BwdAcc &acc) {
+template <bool kTest, bool kClamp>
+__device__ __forceinline__ void bwd_rows(const BwdSplat &bs, const TileState &S, int rlo, int rhi, BwdAcc &acc) {
     const float2 zero2 = make_float2(0.f, 0.f);
     for (int ky = rlo; ky <= rhi; ++ky) {
-        const RowTerms rt = row_terms(bs.A2dx0, bs.dy0, bs.rA2, bs.B2, ky);
-        const float2 e10p = make_float2(rt.e10, rt.e10), e2p = make_float2(rt.e2sq, rt.e2sq);
+        const RowTerms rt = row_terms(bs.A2dx0, bs.dy0, bs.rA2, bs.B2, bs.log2o, ky);
+        const float2 e10p = make_float2(rt.e10, rt.e10), lrp = make_float2(rt.lrow, rt.lrow);
         float2 Rd = zero2, Re = zero2;
 #pragma unroll
-        for (int kq0 = 0; kq0 < kTile / 4; kq0 += kQuads) {
-            float2 e1[2 * kQuads], sq[2 * kQuads];
-            bool in[4 * kQuads];
+        for (int m0 = 0; m0 < kTile / 2; m0 += 4) {
+            float2 e1[4], lg[4];
+            bool in[8];
             bool any = false;
 #pragma unroll
-            for (int h = 0; h < 2 * kQuads; ++h) {
-                const float kx = (float)(4 * kq0 + 2 * h);
+            for (int h = 0; h < 4; ++h) {
+                const float kx = (float)(2 * (m0 + h));
                 e1[h] = __ffma2_rn(bs.A2p, make_float2(kx, kx + 1.f), e10p);
-                sq[h] = __ffma2_rn(e1[h], e1[h], e2p);
-                in[2 * h] = !kTest || sq[h].x <= bs.thr;
-                in[2 * h + 1] = !kTest || sq[h].y <= bs.thr;
+                lg[h] = pair_lg2(e1[h], lrp);
+                in[2 * h] = !kTest || lg[h].x >= kMinLog2Alpha;
+                in[2 * h + 1] = !kTest || lg[h].y >= kMinLog2Alpha;
                 any = any || in[2 * h] || in[2 * h + 1];
             }
             if (!kTest || __any_sync(0xffffffffu, any)) {
 #pragma unroll
-                for (int qq = 0; qq < kQuads; ++qq) {
-                    const int kq = ky * (kTile / 4) + kq0 + qq;
-                    const float4 u0 = S.p[0][kq], u1 = S.p[1][kq], u2 = S.p[2][kq], u3 = S.p[3][kq];
-                    const float4 u4 = S.p[4][kq];
-                    bwd_step<kClamp>(bs, e1[2 * qq], sq[2 * qq], in[4 * qq], in[4 * qq + 1], make_float2(u0.x, u0.y),
-                                     make_float2(u1.x, u1.y), make_float2(u2.x, u2.y), make_float2(u3.x, u3.y),
-                                     make_float2(u4.x, u4.y), Rd, Re, acc);
-                    bwd_step<kClamp>(bs, e1[2 * qq + 1], sq[2 * qq + 1], in[4 * qq + 2], in[4 * qq + 3],
-                                     make_float2(u0.z, u0.w), make_float2(u1.z, u1.w), make_float2(u2.z, u2.w),
-                                     make_float2(u3.z, u3.w), make_float2(u4.z, u4.w), Rd, Re, acc);
+                for (int h = 0; h < 4; h += 2) {
+                    PixPair p0, p1;
+                    S.get2(ky, m0 + h, p0, p1);
+                    bwd_step<kClamp>(bs, e1[h], lg[h], in[2 * h], in[2 * h + 1], p0, Rd, Re, acc);
+                    bwd_step<kClamp>(bs, e1[h + 1], lg[h + 1], in[2 * h + 2], in[2 * h + 3], p1, Rd, Re, acc);
                 }
             }
         }
@@ -152,159 +177,167 @@ __device__ __forceinline__ void bwd_rows(const BwdSplat &bs, const BwdState &S, 
     }
 }
 
-constexpr int kBwdQuads = 2;  // groups of four pixels per warp vote
-// Threads per block (one block per tile).  Each round gives every warp 32 of the tile's splats;
-// four warps keep more of a typical tile's warps busy (the median tile holds ~110 splats at a 5 %
-// active set) than eight, without stretching the heaviest tiles into long serial chains as two do.
+// One warp's group of 32 splats (record indices q; >= nrec: no splat) over the tile.
+__device__ __forceinline__ void bwd_group(const float4 *__restrict__ rec, uint32_t q, uint32_t nrec, float ox,
+                                          float oy, const TileState &S, float4 *__restrict__ sgrad) {
+    const bool valid = q < nrec;
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 1.f), a1 = make_float4(0.f, -INFINITY, 0.f, -1.f);
+    float4 a2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+        a0 = rec[3 * (int64_t)q + 0];
+        a1 = rec[3 * (int64_t)q + 1];
+        a2 = rec[3 * (int64_t)q + 2];
+    }
+    const float rr = a0.z, A2 = a0.w, B2 = a1.x, log2o = a1.y, w = a1.z, yh = a1.w;
+    const SplatConsts sc = splat_consts(ox, oy, a0.x, a0.y, rr, A2);
+    // rows of the tile this lane's ellipse can reach; the warp walks their union
+    int rlo = kTile, rhi = -1;
+    if (valid && yh >= 0.f) {
+        rlo = f2i_clamped(ceilf(-yh - sc.dy0), 0, kTile);
+        rhi = f2i_clamped(floorf(yh - sc.dy0), -1, kTile - 1);
+    }
+    rlo = __reduce_min_sync(0xffffffffu, rlo);
+    rhi = __reduce_max_sync(0xffffffffu, rhi);
+    if (rlo > rhi) return;  // uniform: no lane reaches the tile
+
+    const float2 zero2 = make_float2(0.f, 0.f);
+    BwdAcc acc;
+    acc.See = acc.gw = acc.gc0 = acc.gc1 = acc.gc2 = zero2;
+    acc.Se = acc.Sey = acc.Sd = acc.Sdy = acc.Sdyy = 0.f;
+    const BwdSplat bs{make_float2(A2, A2), make_float2(w, w), make_float2(a2.x, a2.x), make_float2(a2.y, a2.y),
+                      make_float2(a2.z, a2.z), sc.A2dx0, sc.dy0, sc.rA2, B2, log2o};
+    // a splat with log2 o <= kNoClampLog2 never reaches the 0.99 clamp
+    const bool clamp = __any_sync(0xffffffffu, valid && log2o > kNoClampLog2);
+    const bool full = !valid || tile_inside(sc, A2, B2, log2o);
+    if (__all_sync(0xffffffffu, full)) {  // every pixel of the tile contributes
+        if (clamp)
+            bwd_rows<false, true>(bs, S, 0, kTile - 1, acc);
+        else
+            bwd_rows<false, false>(bs, S, 0, kTile - 1, acc);
+    } else if (clamp) {
+        bwd_rows<true, true>(bs, S, rlo, rhi, acc);
+    } else {
+        bwd_rows<true, false>(bs, S, rlo, rhi, acc);
+    }
+    if (valid) {
+        const float K = -2.f * kLn2;
+        const float See1 = acc.See.x + acc.See.y;
+        const float g_mx = -K * A2 * acc.Se;
+        const float g_my = K * (A2 * rr * acc.Se - B2 * B2 * acc.Sdy);
+        const float g_r = -K * A2 * acc.Sey;
+        const float g_A2 = K * See1 / A2;
+        const float g_B2 = K * B2 * acc.Sdyy;
+        float4 *out = sgrad + 3 * (int64_t)q;
+        atomicAdd(out + 0, make_float4(g_mx, g_my, g_r, g_A2));
+        atomicAdd(out + 1, make_float4(g_B2, acc.Sd, acc.gw.x + acc.gw.y, w * (acc.gc0.x + acc.gc0.y)));
+        atomicAdd(reinterpret_cast<float2 *>(out + 2),
+                  make_float2(w * (acc.gc1.x + acc.gc1.y), w * (acc.gc2.x + acc.gc2.y)));
+    }
+}
+
+// Sort key of a pair (ascending): 0 when the splat's cutoff ellipse contains
+// the whole tile, else 1 + the first tile row its ellipse reaches.
+constexpr int kBwdKeys = kTile + 1;
+__device__ __forceinline__ int pair_key(const float4 *rec, uint32_t q, float ox, float oy) {
+    const float4 a0 = rec[3 * (int64_t)q + 0], a1 = rec[3 * (int64_t)q + 1];
+    const float A2 = a0.w, B2 = a1.x, log2o = a1.y, yh = a1.w;
+    const SplatConsts c = splat_consts(ox, oy, a0.x, a0.y, a0.z, A2);
+    if (tile_inside(c, A2, B2, log2o)) return 0;
+    return 1 + f2i_clamped(ceilf(-yh - c.dy0), 0, kTile - 1);
+}
+
+constexpr int kBwdChunk = 1024;  // pairs sorted together (the heaviest tile of 1M splats / 5 % holds ~900)
+// Threads per block (one block per tile): four warps keep more of a typical tile's warps busy
+// (the median tile holds ~110 splats at a 5 % active set) than eight, without stretching the
+// heaviest tiles into long serial chains as two do.
 constexpr int kBwdThreads = 128;
 constexpr int kBwdMinBlocks = 12 * 64 / kBwdThreads;  // <= 85 registers a thread
 
-template <bool kGroup>
-__global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) raster_bwd_kernel(const __grid_constant__ Batch b,
-                                                              const float4 *__restrict__ rec,
-                                                              const int *__restrict__ offsets,
-                                                              const uint32_t *__restrict__ pairs, int64_t cap,
-                                                              uint32_t nrec, float4 *__restrict__ sgrad) {
-    __shared__ BwdState S;
-    __shared__ uint32_t sorted[kGroup ? kBwdThreads : 1];
-    __shared__ uint8_t sfull[kGroup ? kBwdThreads : 1];
-    __shared__ int hist[kBwdKeys];
+// kSort: each chunk of up to kBwdChunk of the tile's pairs is counting-sorted in shared memory
+// by pair_key before the warps take groups of 32 from a shared counter (else the warps take the
+// pairs in arena order).
+template <bool kSort>
+__global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks)
+    raster_bwd_kernel(const __grid_constant__ Batch b, const float4 *__restrict__ rec,
+                      const int *__restrict__ offsets, const uint32_t *__restrict__ pairs, int64_t cap,
+                      uint32_t nrec, float4 *__restrict__ sgrad, int *queue) {
+    __shared__ TileState S;
+    __shared__ uint32_t sorted[kSort ? kBwdChunk : 1];
+    __shared__ uint16_t slot[kSort ? kBwdChunk : 1];
+    __shared__ uint8_t keys[kSort ? kBwdChunk : 1];
+    __shared__ int hist[32];
+    __shared__ int next_group;
 
-    const int gt = block_tile(b);
-    const int v = find_view(b, gt);
-    const ViewDesc &vd = b.v[v];
-    const int lt = gt - vd.tile_base;
-    const int ty = lt / vd.tiles_x, tx = lt - ty * vd.tiles_x;
-    const int tid = threadIdx.x;
-#pragma unroll
-    for (int t = tid; t < kTilePix; t += kBwdThreads) {
-        const int x = tx * kTile + (t & (kTile - 1)), y = ty * kTile + (t >> 4);
-        float st5[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        if (x < vd.W && y < vd.H) {
-            const int64_t HW = (int64_t)vd.W * vd.H, pix = (int64_t)y * vd.W + x;
-            const float *st = vd.state;
-#pragma unroll
-            for (int k = 0; k < 5; ++k) st5[k] = st[k * HW + pix];
-        }
-#pragma unroll
-        for (int k = 0; k < 5; ++k) reinterpret_cast<float *>(S.p[k])[t] = st5[k];
-    }
-    __syncthreads();
-
-    const int start = offsets[gt];
-    const int end = (int)min((int64_t)offsets[gt + 1], cap);
-    const int warp = tid >> 5, lane = tid & 31;
-    const float ox = (float)(tx * kTile) + 0.5f, oy = (float)(ty * kTile) + 0.5f;
-
-    for (int cb0 = start; cb0 < end; cb0 += kBwdThreads) {
-        uint32_t q;
-        bool full = false;
-        if (kGroup) {
-            // rank this round's splats: class 0 = the whole tile lies inside the cutoff ellipse (its
-            // four corner pixels do, by a margin; the ellipse is convex, so then every pixel does
-            // and its rounded exponent stays below the cut), classes 1-16 = the 4x4-pixel cell of
-            // the centre (clamped), 17 = no record; then warps take 32 consecutive splats
-            const int nr = min(kBwdThreads, end - cb0);
-            uint32_t myq = 0xffffffffu;
-            int key = kBwdKeys - 1, slot = 0;
-            if (tid < kBwdKeys) hist[tid] = 0;
+    __shared__ int item_s;
+    if (bin_failed(b)) return;  // the binning scan gave up: offsets and tile order are incomplete
+    // queue == null: this block's tile (block_tile); else a persistent block that takes tiles from the
+    // queue (in the raster order) until none is left
+    for (int it = 0;; ++it) {
+        int gt;
+        if (queue) {
+            if (threadIdx.x == 0) item_s = atomicAdd(queue, 1);
+            __syncthreads();  // also: every warp is done with the previous tile
+            const int item = item_s;
             __syncthreads();
-            if (tid < nr) {
-                myq = pairs[cb0 + tid];
-                if (myq < nrec) {
-                    const float4 c0r = rec[3 * (int64_t)myq + 0], c1r = rec[3 * (int64_t)myq + 1];
-                    const SplatConsts k = splat_consts(ox, oy, c0r.x, c0r.y, c0r.z, c0r.w, c1r.y);
-                    const float lim = k.thr - fmaf(1e-3f, fabsf(k.thr), 1e-3f);
-                    bool in = true;
-#pragma unroll
-                    for (int cyy = 0; cyy < 2; ++cyy) {
-                        const RowTerms rt = row_terms(k.A2dx0, k.dy0, k.rA2, c1r.x, cyy * (kTile - 1));
-#pragma unroll
-                        for (int cxx = 0; cxx < 2; ++cxx)
-                            in = in && quad_s(col_e1(c0r.w, rt.e10, cxx * (kTile - 1)), rt.e2sq) <= lim;
+            if (item >= b.total_tiles) break;
+            gt = b.tile_order ? __ldg(b.tile_order + item) : item;
+        } else {
+            if (it > 0) break;
+            gt = block_tile(b);
+        }
+        const int v = find_view(b, gt);
+        const ViewDesc &vd = b.v[v];
+        const int lt = gt - vd.tile_base;
+        const int ty = lt / vd.tiles_x, tx = lt - ty * vd.tiles_x;
+        const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+        load_tile_state<kBwdThreads>(vd, tx, ty, S);
+
+        const int start = offsets[gt];
+        const int end = (int)min((int64_t)offsets[gt + 1], cap);
+        const float ox = (float)(tx * kTile) + 0.5f, oy = (float)(ty * kTile) + 0.5f;
+
+        if constexpr (!kSort) {
+            __syncthreads();
+            for (int cb0 = start + warp * 32; cb0 < end; cb0 += kBwdThreads) {
+                const int idx = cb0 + lane;
+                bwd_group(rec, idx < end ? pairs[idx] : 0xffffffffu, nrec, ox, oy, S, sgrad);
+            }
+        } else {
+            for (int c0 = start; c0 < end; c0 += kBwdChunk) {
+                const int nc = min(kBwdChunk, end - c0);
+                if (c0 > start) __syncthreads();  // the previous chunk's arrays are consumed
+                if (tid < 32) hist[tid] = 0;
+                if (tid == 0) next_group = 0;
+                __syncthreads();  // also: the state is loaded
+                for (int i = tid; i < nc; i += kBwdThreads) {
+                    const uint32_t q = pairs[c0 + i];
+                    const int key = q < nrec ? pair_key(rec, q, ox, oy) : kBwdKeys - 1;
+                    keys[i] = (uint8_t)key;
+                    slot[i] = (uint16_t)atomicAdd(&hist[key], 1);
+                }
+                __syncthreads();
+                if (warp == 0) {  // first position of each key
+                    const int h = hist[lane];
+                    int incl = h;
+    #pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, incl, off);
+                        if (lane >= off) incl += y;
                     }
-                    const int cx = f2i_clamped(floorf((c0r.x - (ox - 0.5f)) * 0.25f), 0, 3);
-                    const int cy = f2i_clamped(floorf((c0r.y - (oy - 0.5f)) * 0.25f), 0, 3);
-                    key = in ? 0 : 1 + cy * 4 + cx;
+                    hist[lane] = incl - h;
                 }
-                slot = atomicAdd(&hist[key], 1);
-            }
-            __syncthreads();
-            if (tid == 0) {
-                int run = 0;
-                for (int c = 0; c < kBwdKeys; ++c) {
-                    const int t = hist[c];
-                    hist[c] = run;
-                    run += t;
+                __syncthreads();
+                for (int i = tid; i < nc; i += kBwdThreads) sorted[hist[keys[i]] + slot[i]] = pairs[c0 + i];
+                __syncthreads();
+                for (;;) {
+                    int g = 0;
+                    if (lane == 0) g = atomicAdd(&next_group, 1);
+                    g = __shfl_sync(0xffffffffu, g, 0);
+                    const int idx = g * 32 + lane;
+                    if (g * 32 >= nc) break;  // uniform over the warp
+                    bwd_group(rec, idx < nc ? sorted[idx] : 0xffffffffu, nrec, ox, oy, S, sgrad);
                 }
             }
-            __syncthreads();
-            if (tid < nr) {
-                sorted[hist[key] + slot] = myq;
-                sfull[hist[key] + slot] = key == 0 ? 1 : 0;
-            }
-            __syncthreads();
-            const int idx = warp * 32 + lane;
-            q = idx < nr ? sorted[idx] : 0xffffffffu;
-            full = idx < nr && sfull[idx] != 0;
-            if (cb0 + warp * 32 >= end) continue;  // this warp has no splat in this round
-        } else {
-            const int idx = cb0 + warp * 32 + lane;
-            if (cb0 + warp * 32 >= end) continue;
-            q = idx < end ? pairs[idx] : 0xffffffffu;
-        }
-        const bool valid = q < nrec;
-        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = make_float4(0.f, -INFINITY, 0.f, -1.f), a2 = a0;
-        if (valid) {
-            a0 = rec[3 * (int64_t)q + 0];
-            a1 = rec[3 * (int64_t)q + 1];
-            a2 = rec[3 * (int64_t)q + 2];
-        }
-        const float rr = a0.z, A2 = a0.w, B2 = a1.x, log2o = a1.y, w = a1.z, yh = a1.w;
-        const SplatConsts sc = splat_consts(ox, oy, a0.x, a0.y, rr, A2, log2o);
-        const float dy0 = sc.dy0;
-        // rows of the tile this lane's ellipse can reach; the warp walks their union
-        int rlo = kTile, rhi = -1;
-        if (valid && yh >= 0.f) {
-            rlo = f2i_clamped(ceilf(-yh - dy0), 0, kTile);
-            rhi = f2i_clamped(floorf(yh - dy0), -1, kTile - 1);
-        }
-        rlo = __reduce_min_sync(0xffffffffu, rlo);
-        rhi = __reduce_max_sync(0xffffffffu, rhi);
-
-        const float2 A2p = make_float2(A2, A2), wp = make_float2(w, w), l2op = make_float2(log2o, log2o);
-        const float2 c0p = make_float2(a2.x, a2.x), c1p = make_float2(a2.y, a2.y), c2p = make_float2(a2.z, a2.z);
-        const float2 zero2 = make_float2(0.f, 0.f);
-        BwdAcc acc;
-        acc.See = acc.gw = acc.gc0 = acc.gc1 = acc.gc2 = zero2;
-        acc.Se = acc.Sey = acc.Sd = acc.Sdy = acc.Sdyy = 0.f;
-        const BwdSplat bs{A2p, wp, l2op, c0p, c1p, c2p, sc.A2dx0, dy0, sc.rA2, B2, sc.thr};
-        // a splat with log2 o <= kNoClampLog2 never reaches the 0.99 clamp
-        const bool clamp = __any_sync(0xffffffffu, valid && log2o > kNoClampLog2);
-        if (kGroup && __all_sync(0xffffffffu, full || !valid)) {  // every pixel of the tile contributes
-            if (clamp)
-                bwd_rows<false, true, kBwdQuads>(bs, S, 0, kTile - 1, acc);
-            else
-                bwd_rows<false, false, kBwdQuads>(bs, S, 0, kTile - 1, acc);
-        } else if (clamp) {
-            bwd_rows<true, true, kBwdQuads>(bs, S, rlo, rhi, acc);
-        } else {
-            bwd_rows<true, false, kBwdQuads>(bs, S, rlo, rhi, acc);
-        }
-        const float Se = acc.Se, Sey = acc.Sey, Sd = acc.Sd, Sdy = acc.Sdy, Sdyy = acc.Sdyy;
-        const float2 See = acc.See, gw = acc.gw, gc0 = acc.gc0, gc1 = acc.gc1, gc2 = acc.gc2;
-        if (valid) {
-            const float K = -2.f * kLn2;
-            const float See1 = See.x + See.y;
-            const float g_mx = -K * A2 * Se;
-            const float g_my = K * (A2 * rr * Se - B2 * B2 * Sdy);
-            const float g_r = -K * A2 * Sey;
-            const float g_A2 = K * See1 / A2;
-            const float g_B2 = K * B2 * Sdyy;
-            float4 *out = sgrad + 3 * (int64_t)q;
-            atomicAdd(out + 0, make_float4(g_mx, g_my, g_r, g_A2));
-            atomicAdd(out + 1, make_float4(g_B2, Sd, gw.x + gw.y, w * (gc0.x + gc0.y)));
-            atomicAdd(reinterpret_cast<float2 *>(out + 2), make_float2(w * (gc1.x + gc1.y), w * (gc2.x + gc2.y)));
         }
     }
 }
@@ -336,14 +369,31 @@ int launch_prep_state(const Batch &b, const float bg[3], cudaStream_t st) {
     return 0;
 }
 
-int launch_raster_bwd(const Batch &b, bool group, const float4 *rec, const int *offsets, const uint32_t *pairs,
-                      int64_t cap, float4 *sgrad, cudaStream_t st) {
+template <bool kSort>
+static void launch_bwd(const Batch &b, const float4 *rec, const int *offsets, const uint32_t *pairs, int64_t cap,
+                       uint32_t nrec, float4 *sgrad, int *queue, cudaStream_t st) {
+    auto kern = raster_bwd_kernel<kSort>;
+    int grid = b.total_tiles;
+    if (queue) {  // persistent: as many blocks as fit on the device at once, at most one per tile
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBwdThreads, 0);
+        const int g = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+        grid = g < grid ? g : grid;
+        cudaMemsetAsync(queue, 0, sizeof(int), st);
+    }
+    kern<<<grid, kBwdThreads, 0, st>>>(b, rec, offsets, pairs, cap, nrec, sgrad, queue);
+}
+
+int launch_raster_bwd(const Batch &b, int walk, const float4 *rec, const int *offsets, const uint32_t *pairs,
+                      int64_t cap, float4 *sgrad, int *queue, cudaStream_t st) {
     if (b.total_tiles == 0) return 0;
     const uint32_t nrec = (uint32_t)((int64_t)b.n_views * b.n_list);
-    if (group)
-        raster_bwd_kernel<true><<<b.total_tiles, kBwdThreads, 0, st>>>(b, rec, offsets, pairs, cap, nrec, sgrad);
+    if (walk == kBwdWalkArena)
+        launch_bwd<false>(b, rec, offsets, pairs, cap, nrec, sgrad, queue, st);
     else
-        raster_bwd_kernel<false><<<b.total_tiles, kBwdThreads, 0, st>>>(b, rec, offsets, pairs, cap, nrec, sgrad);
+        launch_bwd<true>(b, rec, offsets, pairs, cap, nrec, sgrad, queue, st);
     return 0;
 }
 

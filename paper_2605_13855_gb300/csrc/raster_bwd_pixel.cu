@@ -27,10 +27,11 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_pixel_kernel(const __grid
                                                                     const int *__restrict__ offsets,
                                                                     const uint32_t *__restrict__ pairs, int64_t cap,
                                                                     uint32_t nrec, float4 *__restrict__ sgrad) {
-    // staged per splat: s0 = (A2 dx0, dy0, r A2, A2), s1 = (B2, thr, log2 o, w), s2 = (c_r, c_g, c_b, r)
+    // staged per splat: s0 = (A2 dx0, dy0, r A2, A2), s1 = (B2, 0, log2 o, w), s2 = (c_r, c_g, c_b, r)
     __shared__ float4 s0[kPixBatch], s1[kPixBatch], s2[kPixBatch];
     __shared__ uint32_t sq[kPixBatch];
 
+    if (bin_failed(b)) return;  // the binning scan gave up: offsets and tile order are incomplete
     const int gt = block_tile(b);
     const int v = find_view(b, gt);
     const ViewDesc &vd = b.v[v];
@@ -61,14 +62,14 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_pixel_kernel(const __grid
         __syncthreads();
         if (tid < n) {
             const uint32_t q = pairs[base + tid];
-            float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = make_float4(0.f, -INFINITY, 0.f, 0.f), t2 = t0;
+            float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = make_float4(0.f, 0.f, -INFINITY, 0.f), t2 = t0;
             if (q < nrec) {
                 const float4 a0 = rec[3 * (int64_t)q + 0];
                 const float4 a1 = rec[3 * (int64_t)q + 1];
                 const float4 a2 = rec[3 * (int64_t)q + 2];
-                const SplatConsts c = splat_consts(ox, oy, a0.x, a0.y, a0.z, a0.w, a1.y);
+                const SplatConsts c = splat_consts(ox, oy, a0.x, a0.y, a0.z, a0.w);
                 t0 = make_float4(c.A2dx0, c.dy0, c.rA2, a0.w);
-                t1 = make_float4(a1.x, c.thr, a1.y, a1.z);
+                t1 = make_float4(a1.x, 0.f, a1.y, a1.z);
                 t2 = make_float4(a2.x, a2.y, a2.z, a0.z);
             }
             s0[tid] = t0;
@@ -79,17 +80,17 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_pixel_kernel(const __grid
         __syncthreads();
         for (int j = 0; j < n; ++j) {
             const float4 a0 = s0[j], a1 = s1[j];
-            const RowTerms rt = row_terms(a0.x, a0.y, a0.z, a1.x, ky);
+            const RowTerms rt = row_terms(a0.x, a0.y, a0.z, a1.x, a1.z, ky);
             const float e1 = col_e1(a0.w, rt.e10, kx);
-            const float s = quad_s(e1, rt.e2sq);
-            const bool in = s <= a1.y;
+            const float lg = pair_lg(e1, rt.lrow);
+            const bool in = lg >= kMinLog2Alpha;
             if (!__any_sync(0xffffffffu, in)) continue;
             float v10[10];
 #pragma unroll
             for (int k = 0; k < 10; ++k) v10[k] = 0.f;
             if (in) {
                 const float4 a2 = s2[j];
-                const float ar = fast_exp2(a1.z - s);
+                const float ar = fast_exp2(lg);
                 const float a = fminf(ar, kAlphaMax);
                 const float am = ar > kAlphaMax ? 0.f : a;
                 const float D = fmaf(Bg0, a2.x, fmaf(Bg1, a2.y, fmaf(Bg2, a2.z, nBgF)));

@@ -1,8 +1,8 @@
 // raster_fwd.cu -- tile rasteriser of the OIT sums (Alg. 2 BAN / BAU, Eq. 7).
 //
 // One block per 16x16 tile; each thread owns a 1xS strip of pixels of one
-// row (S = 1, 2 or 4, a launch parameter; the exponent of the next pixel of
-// the strip costs one FMA), each warp owns 2S rows.  The tile's records are
+// row (S = 1, 2 or 4, a launch parameter; the exponent of each pixel of the
+// strip costs two FMAs), each warp owns 2S rows.  The tile's records are
 // staged through shared memory 256 at a time, already shifted to
 // tile-relative offsets, and sorted by warp ballots into one list of the
 // records whose cutoff ellipse contains the whole tile (evaluated without
@@ -28,25 +28,19 @@ namespace soit {
 constexpr int kFwdBatch = 256;    // records staged per round
 constexpr int kFwdUnroll = 2;     // records per iteration of the accumulation loop
 
-// The strip's quadratics s = e1^2 + e2^2 and log2 alpha_raw = log2 o - s, two
-// pixels per f32x2 instruction where the strip has pairs (each component
-// rounds like the scalar FMA, so the decisions match the backward's).
+// The strip's exponents log2 alpha_raw = lrow - e1^2, two pixels per f32x2
+// instruction where the strip has pairs (each component rounds like the
+// scalar FMA, so the decisions match the backward's).
 template <int kStrip>
-__device__ __forceinline__ void strip_exponents(float A2, float e10, float e2sq, float log2o, int sx, float *sq,
-                                                float *lg) {
+__device__ __forceinline__ void strip_exponents(float A2, float e10, float lrow, int sx, float *lg) {
     if (kStrip == 1) {
-        sq[0] = quad_s(col_e1(A2, e10, sx), e2sq);
-        lg[0] = log2o - sq[0];
+        lg[0] = pair_lg(col_e1(A2, e10, sx), lrow);
     } else {
-        const float2 A2p = make_float2(A2, A2), e10p = make_float2(e10, e10), e2p = make_float2(e2sq, e2sq);
-        const float2 l2p = make_float2(log2o, log2o), m1 = make_float2(-1.f, -1.f);
+        const float2 A2p = make_float2(A2, A2), e10p = make_float2(e10, e10), lrp = make_float2(lrow, lrow);
 #pragma unroll
         for (int p = 0; p < kStrip; p += 2) {
             const float2 e1 = __ffma2_rn(A2p, make_float2((float)(sx + p), (float)(sx + p + 1)), e10p);
-            const float2 q = __ffma2_rn(e1, e1, e2p);
-            const float2 l = __ffma2_rn(q, m1, l2p);  // -s + log2 o: one rounding, as the subtraction
-            sq[p] = q.x;
-            sq[p + 1] = q.y;
+            const float2 l = pair_lg2(e1, lrp);
             lg[p] = l.x;
             lg[p + 1] = l.y;
         }
@@ -63,12 +57,12 @@ __device__ __forceinline__ void fwd_splat(const float4 *s0, const float4 *s1, co
                                           float2 *b2q, float *bl, float *T, unsigned &n_contrib) {
     const float4 a0 = s0[j], a1 = s1[j], a2 = s2[j];
     const bool counted = kCount && j < kFwdBatch && in_view_row;  // the empty record counts nothing
-    const RowTerms rt = row_terms(a0.x, a0.y, a0.z, a1.x, ky);
-    float sq[kStrip], lg[kStrip];
-    strip_exponents<kStrip>(a0.w, rt.e10, rt.e2sq, a1.z, sx, sq, lg);
+    const RowTerms rt = row_terms(a0.x, a0.y, a0.z, a1.x, a1.z, ky);
+    float lg[kStrip];
+    strip_exponents<kStrip>(a0.w, rt.e10, rt.lrow, sx, lg);
 #pragma unroll
     for (int p = 0; p < kStrip; ++p) {
-        if (!kTest || sq[p] <= a1.y) {
+        if (!kTest || lg[p] >= kMinLog2Alpha) {
             const float ar = fast_exp2(lg[p]);
             const float a = kClamp ? fminf(ar, kAlphaMax) : ar;
             const float2 aa = make_float2(a, a);
@@ -134,7 +128,8 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
                                                                  const int *__restrict__ offsets,
                                                                  const uint32_t *__restrict__ pairs, int64_t cap,
                                                                  uint32_t nrec, float bg0, float bg1, float bg2,
-                                                                 float *loss, unsigned long long *contrib) {
+                                                                 float *loss, unsigned long long *contrib,
+                                                                 int *queue) {
     constexpr int kFwdThreads = kTilePix / kStrip;
     constexpr int kStripsPerRow = kTile / kStrip;
     constexpr int kWarps = kFwdThreads / 32;
@@ -149,231 +144,258 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
     __shared__ float red[kFwdThreads / 32];
     __shared__ unsigned red_n[kFwdThreads / 32];
 
-    const int gt = block_tile(b);
-    const int v = find_view(b, gt);
-    const ViewDesc &vd = b.v[v];
-    const int lt = gt - vd.tile_base;
-    const int ty = lt / vd.tiles_x, tx = lt - ty * vd.tiles_x;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int ky = tid / kStripsPerRow, sx = (tid % kStripsPerRow) * kStrip;
-    const float ox = (float)(tx * kTile) + 0.5f, oy = (float)(ty * kTile) + 0.5f;
-    const bool in_view_row = ty * kTile + ky < vd.H;
-    const int x0 = tx * kTile + sx;
-
-    const int start = offsets[gt];
-    const int end = (int)min((int64_t)offsets[gt + 1], cap);
-
-    if (tid == 0) {
-        s0[kFwdBatch] = make_float4(0.f, 0.f, 0.f, 0.f);
-        s1[kFwdBatch] = make_float4(0.f, -INFINITY, -INFINITY, -1.f);  // log2 o = -inf: alpha 0
-        s2[kFwdBatch] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (kMode == kRasterSums) ssign[kFwdBatch] = 0.f;
-    }
-
-    // per pixel: (P_r, P_g) and (P_b, Q) as f32x2 pairs (one paired FMA per pair of sums;
-    // each component rounds like the scalar FMA), T (log T in sums mode)
-    float2 P01[kStrip], P2Q[kStrip];
-    float T[kStrip];
-#pragma unroll
-    for (int j = 0; j < kStrip; ++j) {
-        P01[j] = P2Q[j] = make_float2(0.f, 0.f);
-        T[j] = kMode == kRasterSums ? 0.f : 1.f;  // log T in sums mode
-    }
-    unsigned n_contrib = 0;
-
-    for (int base = start; base < end; base += kFwdBatch) {
-        const int n = min(kFwdBatch, end - base);
-        __syncthreads();  // the previous batch's records and lists are consumed
-        if (tid == 0) fcnt = 0;
-        if (tid < kWarps) wcnt[tid] = 0;
-        __syncthreads();
-        int may_clamp = 0;  // some staged splat can reach the 0.99 clamp
-        for (int k0 = 0; k0 < n; k0 += kFwdThreads) {  // uniform trip count: the lists use warp ballots
-            const int k = k0 + tid;
-            // staged: s0 = (A2 dx0, dy0, r A2, A2), s1 = (B2, thr, log2 o, yh),
-            //         s2 = (w c_r, w c_g, w c_b, w) (times the sign in sums mode)
-            bool ok = false, full = false;
-            float dy0 = 0.f, yh = -1.f;
-            if (k < n) {
-                const uint32_t q = pairs[base + k];
-                float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = make_float4(0.f, -INFINITY, 0.f, -1.f);
-                float4 t2 = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (q < nrec) {  // never written by this call's scatter otherwise: contributes nothing
-                    const float4 a0 = rec[3 * (int64_t)q + 0];
-                    const float4 a1 = rec[3 * (int64_t)q + 1];
-                    const float4 a2 = rec[3 * (int64_t)q + 2];
-                    const SplatConsts c = splat_consts(ox, oy, a0.x, a0.y, a0.z, a0.w, a1.y);
-                    t0 = make_float4(c.A2dx0, c.dy0, c.rA2, a0.w);
-                    t1 = make_float4(a1.x, c.thr, a1.y, a1.w);
-                    // the whole tile inside the cutoff ellipse: its four corner pixels are, by a margin
-                    // (convexity; the margin keeps every pixel's rounded exponent below the cut)
-                    const float lim = c.thr - fmaf(1e-3f, fabsf(c.thr), 1e-3f);
-                    bool in = true;
-#pragma unroll
-                    for (int cyy = 0; cyy < 2; ++cyy) {
-                        const RowTerms rt = row_terms(c.A2dx0, c.dy0, c.rA2, a1.x, cyy * (kTile - 1));
-#pragma unroll
-                        for (int cxx = 0; cxx < 2; ++cxx)
-                            in = in && quad_s(col_e1(a0.w, rt.e10, cxx * (kTile - 1)), rt.e2sq) <= lim;
-                    }
-                    ok = true;
-                    full = in;
-                    dy0 = c.dy0;
-                    yh = a1.w;
-                    may_clamp |= a1.y > kNoClampLog2 ? 1 : 0;
-                    const float ws = kMode == kRasterSums ? a1.z * a2.w : a1.z;
-                    t2 = make_float4(ws * a2.x, ws * a2.y, ws * a2.z, ws);
-                    if (kMode == kRasterSums) ssign[k] = a2.w;
-                }
-                s0[k] = t0;
-                s1[k] = t1;
-                s2[k] = t2;
-            }
-            list_append(ok && full, k, &fcnt, flist);
-#pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-                // the ellipse's rows |dy0 + ky| <= yh reach rows [w R, w R + R - 1] of the tile
-                const float dlo = dy0 + (float)(w * kRowsPerWarp);
-                const bool hit = ok && !full && !(dlo > yh || dlo + (float)(kRowsPerWarp - 1) < -yh);
-                list_append(hit, k, &wcnt[w], wlist[w]);
-            }
-        }
-        const bool clamp = __syncthreads_or(may_clamp) != 0;
-        const int nf = fcnt, nw = wcnt[warp];
-        if (clamp) {
-            fwd_list<kMode, kCount, kStrip, false, true>(s0, s1, s2, ssign, flist, nf, ky, sx, in_view_row, x0, vd.W,
-                                                         P01, P2Q, T, n_contrib);
-            fwd_list<kMode, kCount, kStrip, true, true>(s0, s1, s2, ssign, wlist[warp], nw, ky, sx, in_view_row, x0,
-                                                        vd.W, P01, P2Q, T, n_contrib);
+    __shared__ int item_s;
+    if (bin_failed(b)) return;  // the binning scan gave up: offsets and tile order are incomplete
+    // queue == null: this block's tile (block_tile); else a persistent block that takes tiles from the
+    // queue (in the raster order) until none is left
+    for (int it = 0;; ++it) {
+        int gt;
+        if (queue) {
+            if (threadIdx.x == 0) item_s = atomicAdd(queue, 1);
+            __syncthreads();
+            const int item = item_s;
+            __syncthreads();  // item_s is read before it is taken again
+            if (item >= b.total_tiles) break;
+            gt = b.tile_order ? __ldg(b.tile_order + item) : item;
         } else {
-            fwd_list<kMode, kCount, kStrip, false, false>(s0, s1, s2, ssign, flist, nf, ky, sx, in_view_row, x0,
-                                                          vd.W, P01, P2Q, T, n_contrib);
-            fwd_list<kMode, kCount, kStrip, true, false>(s0, s1, s2, ssign, wlist[warp], nw, ky, sx, in_view_row, x0,
-                                                         vd.W, P01, P2Q, T, n_contrib);
+            if (it > 0) break;
+            gt = block_tile(b);
         }
-    }
+        const int v = find_view(b, gt);
+        const ViewDesc &vd = b.v[v];
+        const int lt = gt - vd.tile_base;
+        const int ty = lt / vd.tiles_x, tx = lt - ty * vd.tiles_x;
+        const int tid = threadIdx.x, warp = tid >> 5;
+        const int ky = tid / kStripsPerRow, sx = (tid % kStripsPerRow) * kStrip;
+        const float ox = (float)(tx * kTile) + 0.5f, oy = (float)(ty * kTile) + 0.5f;
+        const bool in_view_row = ty * kTile + ky < vd.H;
+        const int x0 = tx * kTile + sx;
 
-    const int64_t HW = (int64_t)vd.W * vd.H;
-    const int y = ty * kTile + ky;
-    float my_loss = 0.f;
-    const float inv3hw = 1.f / (3.f * (float)HW);
-#pragma unroll
-    for (int p = 0; p < kStrip; ++p) {
-        const int x = tx * kTile + sx + p;
-        if (x >= vd.W || y >= vd.H) continue;
-        const int64_t pix = (int64_t)y * vd.W + x;
-        if (kMode == kRasterSums) {
-            float *fz = vd.frozen;
-            fz[pix] += P01[p].x;
-            fz[HW + pix] += P01[p].y;
-            fz[2 * HW + pix] += P2Q[p].x;
-            fz[3 * HW + pix] += P2Q[p].y;
-            fz[4 * HW + pix] += T[p];
-        } else {
-            // the frozen complement's sums (none when the whole set is rendered)
-            const float *fz = vd.frozen;
-            const float f0 = fz ? fz[pix] : 0.f, f1 = fz ? fz[HW + pix] : 0.f, f2 = fz ? fz[2 * HW + pix] : 0.f;
-            const float fq = fz ? fz[3 * HW + pix] : 0.f;
-            const float Pt0 = P01[p].x + f0, Pt1 = P01[p].y + f1, Pt2 = P2Q[p].x + f2;
-            const float Qt = P2Q[p].y + fq;
-            const float Tt = fz ? T[p] * expf(fz[4 * HW + pix]) : T[p];
-            const float invQ = Qt > 0.f ? 1.f / Qt : 0.f;
-            const float F0 = Pt0 * invQ, F1 = Pt1 * invQ, F2 = Pt2 * invQ;
-            const float omT = 1.f - Tt;
-            const float C0 = fmaf(Tt, bg0, omT * F0), C1 = fmaf(Tt, bg1, omT * F1), C2 = fmaf(Tt, bg2, omT * F2);
-            float *img = vd.image + 3 * pix;
-            img[0] = C0;
-            img[1] = C1;
-            img[2] = C2;
-            float *st = vd.state;
-            if (kMode == kRasterFused) {
-                const float *tg = vd.target + 3 * pix;
-                const float d0 = C0 - tg[0], d1 = C1 - tg[1], d2 = C2 - tg[2];
-                my_loss += fabsf(d0) + fabsf(d1) + fabsf(d2);
-                const float g0 = d0 > 0.f ? inv3hw : (d0 < 0.f ? -inv3hw : 0.f);
-                const float g1 = d1 > 0.f ? inv3hw : (d1 < 0.f ? -inv3hw : 0.f);
-                const float g2 = d2 > 0.f ? inv3hw : (d2 < 0.f ? -inv3hw : 0.f);
-                const float B = omT * invQ;
-                st[pix] = B * g0;
-                st[HW + pix] = B * g1;
-                st[2 * HW + pix] = B * g2;
-                st[3 * HW + pix] = Tt * (g0 * (F0 - bg0) + g1 * (F1 - bg1) + g2 * (F2 - bg2));
-                st[4 * HW + pix] = -B * (g0 * F0 + g1 * F1 + g2 * F2);
-            } else {
-                st[pix] = F0;
-                st[HW + pix] = F1;
-                st[2 * HW + pix] = F2;
-                st[3 * HW + pix] = Tt;
-                st[4 * HW + pix] = Qt;
-            }
-        }
-    }
-    if ((kMode == kRasterFused && loss) || kCount) {
-        float l = my_loss;
-        unsigned c = n_contrib;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            l += __shfl_xor_sync(0xffffffffu, l, off);
-            c += __shfl_xor_sync(0xffffffffu, c, off);
-        }
-        if ((tid & 31) == 0) {
-            red[tid >> 5] = l;
-            red_n[tid >> 5] = c;
-        }
-        __syncthreads();
+        const int start = offsets[gt];
+        const int end = (int)min((int64_t)offsets[gt + 1], cap);
+
         if (tid == 0) {
-            float ls = 0.f;
-            unsigned long long cs = 0;
-            for (int k = 0; k < kFwdThreads / 32; ++k) {
-                ls += red[k];
-                cs += red_n[k];
+            s0[kFwdBatch] = make_float4(0.f, 0.f, 0.f, 0.f);
+            s1[kFwdBatch] = make_float4(0.f, 0.f, -INFINITY, -1.f);  // log2 o = -inf: alpha 0
+            s2[kFwdBatch] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (kMode == kRasterSums) ssign[kFwdBatch] = 0.f;
+        }
+
+        // per pixel: (P_r, P_g) and (P_b, Q) as f32x2 pairs (one paired FMA per pair of sums;
+        // each component rounds like the scalar FMA), T (log T in sums mode)
+        float2 P01[kStrip], P2Q[kStrip];
+        float T[kStrip];
+    #pragma unroll
+        for (int j = 0; j < kStrip; ++j) {
+            P01[j] = P2Q[j] = make_float2(0.f, 0.f);
+            T[j] = kMode == kRasterSums ? 0.f : 1.f;  // log T in sums mode
+        }
+        unsigned n_contrib = 0;
+
+        for (int base = start; base < end; base += kFwdBatch) {
+            const int n = min(kFwdBatch, end - base);
+            __syncthreads();  // the previous batch's records and lists are consumed
+            if (tid == 0) fcnt = 0;
+            if (tid < kWarps) wcnt[tid] = 0;
+            __syncthreads();
+            int may_clamp = 0;  // some staged splat can reach the 0.99 clamp
+            for (int k0 = 0; k0 < n; k0 += kFwdThreads) {  // uniform trip count: the lists use warp ballots
+                const int k = k0 + tid;
+                // staged: s0 = (A2 dx0, dy0, r A2, A2), s1 = (B2, 0, log2 o, yh),
+                //         s2 = (w c_r, w c_g, w c_b, w) (times the sign in sums mode)
+                bool ok = false, full = false;
+                float dy0 = 0.f, yh = -1.f;
+                if (k < n) {
+                    const uint32_t q = pairs[base + k];
+                    float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = make_float4(0.f, 0.f, -INFINITY, -1.f);
+                    float4 t2 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (q < nrec) {  // never written by this call's scatter otherwise: contributes nothing
+                        const float4 a0 = rec[3 * (int64_t)q + 0];
+                        const float4 a1 = rec[3 * (int64_t)q + 1];
+                        const float4 a2 = rec[3 * (int64_t)q + 2];
+                        const SplatConsts c = splat_consts(ox, oy, a0.x, a0.y, a0.z, a0.w);
+                        t0 = make_float4(c.A2dx0, c.dy0, c.rA2, a0.w);
+                        t1 = make_float4(a1.x, 0.f, a1.y, a1.w);
+                        ok = true;
+                        // the whole tile inside the cutoff ellipse (its four corner pixels are, by a margin)
+                        full = tile_inside(c, a0.w, a1.x, a1.y);
+                        dy0 = c.dy0;
+                        yh = a1.w;
+                        may_clamp |= a1.y > kNoClampLog2 ? 1 : 0;
+                        const float ws = kMode == kRasterSums ? a1.z * a2.w : a1.z;
+                        t2 = make_float4(ws * a2.x, ws * a2.y, ws * a2.z, ws);
+                        if (kMode == kRasterSums) ssign[k] = a2.w;
+                    }
+                    s0[k] = t0;
+                    s1[k] = t1;
+                    s2[k] = t2;
+                }
+                list_append(ok && full, k, &fcnt, flist);
+    #pragma unroll
+                for (int w = 0; w < kWarps; ++w) {
+                    // the ellipse's rows |dy0 + ky| <= yh reach rows [w R, w R + R - 1] of the tile
+                    const float dlo = dy0 + (float)(w * kRowsPerWarp);
+                    const bool hit = ok && !full && !(dlo > yh || dlo + (float)(kRowsPerWarp - 1) < -yh);
+                    list_append(hit, k, &wcnt[w], wlist[w]);
+                }
             }
-            if (kMode == kRasterFused && loss && ls != 0.f) atomicAdd(loss, ls * inv3hw);
-            if (kCount && contrib && cs) atomicAdd(contrib, cs);
+            const bool clamp = __syncthreads_or(may_clamp) != 0;
+            const int nf = fcnt, nw = wcnt[warp];
+            if (clamp) {
+                fwd_list<kMode, kCount, kStrip, false, true>(s0, s1, s2, ssign, flist, nf, ky, sx, in_view_row, x0, vd.W,
+                                                             P01, P2Q, T, n_contrib);
+                fwd_list<kMode, kCount, kStrip, true, true>(s0, s1, s2, ssign, wlist[warp], nw, ky, sx, in_view_row, x0,
+                                                            vd.W, P01, P2Q, T, n_contrib);
+            } else {
+                fwd_list<kMode, kCount, kStrip, false, false>(s0, s1, s2, ssign, flist, nf, ky, sx, in_view_row, x0,
+                                                              vd.W, P01, P2Q, T, n_contrib);
+                fwd_list<kMode, kCount, kStrip, true, false>(s0, s1, s2, ssign, wlist[warp], nw, ky, sx, in_view_row, x0,
+                                                             vd.W, P01, P2Q, T, n_contrib);
+            }
+        }
+
+        const int64_t HW = (int64_t)vd.W * vd.H;
+        const int y = ty * kTile + ky;
+        float my_loss = 0.f;
+        const float inv3hw = 1.f / (3.f * (float)HW);
+    #pragma unroll
+        for (int p = 0; p < kStrip; ++p) {
+            const int x = tx * kTile + sx + p;
+            if (x >= vd.W || y >= vd.H) continue;
+            const int64_t pix = (int64_t)y * vd.W + x;
+            if (kMode == kRasterSums) {
+                float *fz = vd.frozen;
+                fz[pix] += P01[p].x;
+                fz[HW + pix] += P01[p].y;
+                fz[2 * HW + pix] += P2Q[p].x;
+                fz[3 * HW + pix] += P2Q[p].y;
+                fz[4 * HW + pix] += T[p];
+            } else {
+                // the frozen complement's sums (none when the whole set is rendered)
+                const float *fz = vd.frozen;
+                const float f0 = fz ? fz[pix] : 0.f, f1 = fz ? fz[HW + pix] : 0.f, f2 = fz ? fz[2 * HW + pix] : 0.f;
+                const float fq = fz ? fz[3 * HW + pix] : 0.f;
+                const float Pt0 = P01[p].x + f0, Pt1 = P01[p].y + f1, Pt2 = P2Q[p].x + f2;
+                const float Qt = P2Q[p].y + fq;
+                const float Tt = fz ? T[p] * expf(fz[4 * HW + pix]) : T[p];
+                const float invQ = Qt > 0.f ? 1.f / Qt : 0.f;
+                const float F0 = Pt0 * invQ, F1 = Pt1 * invQ, F2 = Pt2 * invQ;
+                const float omT = 1.f - Tt;
+                const float C0 = fmaf(Tt, bg0, omT * F0), C1 = fmaf(Tt, bg1, omT * F1), C2 = fmaf(Tt, bg2, omT * F2);
+                float *img = vd.image + 3 * pix;
+                img[0] = C0;
+                img[1] = C1;
+                img[2] = C2;
+                float *st = vd.state;
+                if (kMode == kRasterFused) {
+                    const float *tg = vd.target + 3 * pix;
+                    const float d0 = C0 - tg[0], d1 = C1 - tg[1], d2 = C2 - tg[2];
+                    my_loss += fabsf(d0) + fabsf(d1) + fabsf(d2);
+                    const float g0 = d0 > 0.f ? inv3hw : (d0 < 0.f ? -inv3hw : 0.f);
+                    const float g1 = d1 > 0.f ? inv3hw : (d1 < 0.f ? -inv3hw : 0.f);
+                    const float g2 = d2 > 0.f ? inv3hw : (d2 < 0.f ? -inv3hw : 0.f);
+                    const float B = omT * invQ;
+                    st[pix] = B * g0;
+                    st[HW + pix] = B * g1;
+                    st[2 * HW + pix] = B * g2;
+                    st[3 * HW + pix] = Tt * (g0 * (F0 - bg0) + g1 * (F1 - bg1) + g2 * (F2 - bg2));
+                    st[4 * HW + pix] = -B * (g0 * F0 + g1 * F1 + g2 * F2);
+                } else {
+                    st[pix] = F0;
+                    st[HW + pix] = F1;
+                    st[2 * HW + pix] = F2;
+                    st[3 * HW + pix] = Tt;
+                    st[4 * HW + pix] = Qt;
+                }
+            }
+        }
+        if ((kMode == kRasterFused && loss) || kCount) {
+            float l = my_loss;
+            unsigned c = n_contrib;
+    #pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                l += __shfl_xor_sync(0xffffffffu, l, off);
+                c += __shfl_xor_sync(0xffffffffu, c, off);
+            }
+            if ((tid & 31) == 0) {
+                red[tid >> 5] = l;
+                red_n[tid >> 5] = c;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                float ls = 0.f;
+                unsigned long long cs = 0;
+                for (int k = 0; k < kFwdThreads / 32; ++k) {
+                    ls += red[k];
+                    cs += red_n[k];
+                }
+                if (kMode == kRasterFused && loss && ls != 0.f) atomicAdd(loss, ls * inv3hw);
+                if (kCount && contrib && cs) atomicAdd(contrib, cs);
+            }
         }
     }
+}
+
+// Persistent launch: as many blocks as fit on the device at once (occupancy x SMs), at most one per tile.
+template <typename K>
+static int persistent_grid(K kernel, int threads, int total_tiles) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+    const int g = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    return g < total_tiles ? g : total_tiles;
+}
+
+template <int kMode, bool kCount, int kStrip>
+static void launch_one(const Batch &b, const float4 *rec, const int *offsets, const uint32_t *pairs, int64_t cap,
+                       uint32_t nrec, const float bg[3], float *loss, unsigned long long *contrib, int *queue,
+                       cudaStream_t st) {
+    constexpr int kThreads = kTilePix / kStrip;
+    auto kern = raster_fwd_kernel<kMode, kCount, kStrip>;
+    const int grid = queue ? persistent_grid(kern, kThreads, b.total_tiles) : b.total_tiles;
+    kern<<<grid, kThreads, 0, st>>>(b, rec, offsets, pairs, cap, nrec, bg[0], bg[1], bg[2], loss, contrib, queue);
 }
 
 template <int kMode, int kStrip>
 static void launch_strip(const Batch &b, bool count, const float4 *rec, const int *offsets, const uint32_t *pairs,
                          int64_t cap, uint32_t nrec, const float bg[3], float *loss, unsigned long long *contrib,
-                         cudaStream_t st) {
-    const dim3 grid(b.total_tiles), block(kTilePix / kStrip);
+                         int *queue, cudaStream_t st) {
     if (count)
-        raster_fwd_kernel<kMode, true, kStrip><<<grid, block, 0, st>>>(b, rec, offsets, pairs, cap, nrec, bg[0], bg[1],
-                                                                        bg[2], loss, contrib);
+        launch_one<kMode, true, kStrip>(b, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, st);
     else
-        raster_fwd_kernel<kMode, false, kStrip><<<grid, block, 0, st>>>(b, rec, offsets, pairs, cap, nrec, bg[0],
-                                                                         bg[1], bg[2], loss, contrib);
+        launch_one<kMode, false, kStrip>(b, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, st);
 }
 
 template <int kMode>
 static void launch_mode(const Batch &b, int strip, bool count, const float4 *rec, const int *offsets,
                         const uint32_t *pairs, int64_t cap, uint32_t nrec, const float bg[3], float *loss,
-                        unsigned long long *contrib, cudaStream_t st) {
+                        unsigned long long *contrib, int *queue, cudaStream_t st) {
     if (strip == 4)
-        launch_strip<kMode, 4>(b, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, st);
+        launch_strip<kMode, 4>(b, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, st);
     else if (strip == 2)
-        launch_strip<kMode, 2>(b, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, st);
+        launch_strip<kMode, 2>(b, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, st);
     else
-        launch_strip<kMode, 1>(b, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, st);
+        launch_strip<kMode, 1>(b, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, st);
 }
 
 int launch_raster_fwd(const Batch &b, int mode, int strip, const float4 *rec, const int *offsets,
                       const uint32_t *pairs, int64_t cap, const float bg[3], float *loss, unsigned long long *contrib,
-                      cudaStream_t st) {
+                      int *queue, cudaStream_t st) {
     if (b.total_tiles == 0) return 0;
     const uint32_t nrec = (uint32_t)((int64_t)b.n_views * b.n_list);
     const bool count = contrib != nullptr;
+    if (queue) cudaMemsetAsync(queue, 0, sizeof(int), st);
     switch (mode) {
         case kRasterFused:
-            launch_mode<kRasterFused>(b, strip, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, st);
+            launch_mode<kRasterFused>(b, strip, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, st);
             break;
         case kRasterAux:
-            launch_mode<kRasterAux>(b, strip, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, st);
+            launch_mode<kRasterAux>(b, strip, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, st);
             break;
         default:
-            launch_mode<kRasterSums>(b, strip, false, rec, offsets, pairs, cap, nrec, bg, nullptr, nullptr, st);
+            launch_mode<kRasterSums>(b, strip, false, rec, offsets, pairs, cap, nrec, bg, nullptr, nullptr, queue,
+                                     st);
             break;
     }
     return 0;

@@ -114,8 +114,8 @@ class Renderer:
     """A SparseOIT context: active set, per-view frozen sums, batched fwd / bwd."""
 
     def __init__(self, n_splats: int, view_sizes: Sequence[Sequence[int]], max_pairs: int = 0,
-                 fwd_pixels_per_thread: int = 0, proj_lanes_per_splat: int = 0, bwd_group_by_cell: int = 0,
-                 raster_tile_order: int = 0, bwd_parallel: int = 0):
+                 fwd_pixels_per_thread: int = 0, proj_lanes_per_splat: int = 0, bwd_walk: int = 0,
+                 raster_tile_order: int = 0, bwd_parallel: int = 0, raster_persistent: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("sparseoit needs a CUDA device")
         self.lib = _lib.load()
@@ -128,9 +128,10 @@ class Renderer:
         cfg.max_pairs = int(max_pairs)
         cfg.fwd_pixels_per_thread = int(fwd_pixels_per_thread)
         cfg.proj_lanes_per_splat = int(proj_lanes_per_splat)
-        cfg.bwd_group_by_cell = int(bwd_group_by_cell)
+        cfg.bwd_walk = int(bwd_walk)
         cfg.raster_tile_order = int(raster_tile_order)
         cfg.bwd_parallel = int(bwd_parallel)
+        cfg.raster_persistent = int(raster_persistent)
         self._ctx = ctypes.c_void_p()
         rc = self.lib.sparseoit_create(ctypes.byref(self._ctx), self.n, nv, ws, hs, ctypes.byref(cfg))
         if rc != _lib.OK:
@@ -291,9 +292,12 @@ class Renderer:
 
     def autotune(self, splats: SplatParams, cams: Sequence[dict], views: Sequence[int],
                  targets: Optional[Sequence[torch.Tensor]] = None, reps: int = 3, stream=None):
-        """Pick the forward raster's pixels-per-thread for this batch (sparseoit_autotune).
+        """Pick the rasters' launch options for this batch (sparseoit_autotune): the forward strip and
+        whether the forward runs as persistent blocks; with targets also the backward's splat order
+        and persistence.
 
-        Returns {"fwd_pixels_per_thread": chosen, "ms": {candidate: mean forward ms}}."""
+        Returns {"fwd_pixels_per_thread", "ms": {strip: mean forward ms}, "fwd_persistent",
+        "fwd_persistent_ms", "bwd_walk", "bwd_persistent", "bwd_ms": {option: mean backward-raster ms}}."""
         nv = len(views)
         s = splats_struct(splats)
         camarr = (_lib.Camera * nv)(*[camera_struct(c) for c in cams])
@@ -310,8 +314,12 @@ class Renderer:
                                                 ctypes.c_void_p(loss.data_ptr() if loss is not None else 0),
                                                 int(reps), ctypes.byref(t), ctypes.c_void_p(_stream_ptr(stream))))
         self.forward_id += 1
+        names = ("sorted", "arena", "sorted_persistent", "arena_persistent")
         return {"fwd_pixels_per_thread": int(t.fwd_pixels_per_thread),
-                "ms": {int(t.candidates[k]): float(t.ms[k]) for k in range(t.n_candidates)}}
+                "ms": {int(t.candidates[k]): float(t.ms[k]) for k in range(t.n_candidates)},
+                "fwd_persistent": int(t.fwd_persistent), "fwd_persistent_ms": float(t.fwd_persistent_ms),
+                "bwd_walk": int(t.bwd_walk), "bwd_persistent": int(t.bwd_persistent),
+                "bwd_ms": {names[k]: float(t.bwd_ms[k]) for k in range(4)} if t.bwd_walk else {}}
 
     def update_active_set(self, splats: SplatParams, cams: Sequence[dict], targets: Sequence[torch.Tensor],
                           eps: Sequence[float], n_sub: int, first: int, stream=None,
@@ -419,6 +427,11 @@ class Renderer:
     # ------------------------------------------------------------ misc
     def status(self, stream=None):
         self._check(self.lib.sparseoit_status(self._ctx, ctypes.c_void_p(_stream_ptr(stream))))
+
+    def inject_scan_stall(self, partition: int):
+        """Failure injection (tests): the next binning's tile-scan partition `partition` posts
+        nothing, so the later partitions' bounded waits run out (sparseoit_inject_scan_stall)."""
+        self._check(self.lib.sparseoit_inject_scan_stall(self._ctx, int(partition)))
 
     def set_counting(self, enable: bool):
         self._check(self.lib.sparseoit_set_counting(self._ctx, 1 if enable else 0))

@@ -64,10 +64,12 @@ int main(void) {
   F(sparseoit_splats, n) F(sparseoit_splats, rows)
   F(sparseoit_grads, sigma) F(sparseoit_grads, rows_by_splat) F(sparseoit_grads, accumulate)
   F(sparseoit_config, max_pairs) F(sparseoit_config, fwd_pixels_per_thread)
-  F(sparseoit_config, proj_lanes_per_splat) F(sparseoit_config, bwd_group_by_cell) F(sparseoit_config, raster_tile_order) F(sparseoit_config, bwd_parallel)
-  F(sparseoit_config, reserved)
+  F(sparseoit_config, proj_lanes_per_splat) F(sparseoit_config, bwd_walk) F(sparseoit_config, raster_tile_order) F(sparseoit_config, bwd_parallel)
+  F(sparseoit_config, raster_persistent)
   F(sparseoit_kernel_time, launches) F(sparseoit_kernel_time, total_ms)
   F(sparseoit_tuning, n_candidates) F(sparseoit_tuning, candidates) F(sparseoit_tuning, ms)
+  F(sparseoit_tuning, fwd_persistent) F(sparseoit_tuning, fwd_persistent_ms) F(sparseoit_tuning, bwd_walk)
+  F(sparseoit_tuning, bwd_persistent) F(sparseoit_tuning, bwd_ms)
   F(sparseoit_rows, sh_weight) F(sparseoit_rows, sigma)
   F(sparseoit_adam, beta1) F(sparseoit_adam, eps) F(sparseoit_adam, step) F(sparseoit_adam, rows)
   return 0;

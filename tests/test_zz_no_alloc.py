@@ -7,8 +7,9 @@ deployments that forbid allocation after start-up).  Its scratch is a fixed
 device array shared by every call, so this test makes two calls in a row
 with different masks (the second reuses the scratch the first left behind)
 and compares each with the index list of sparseoit_set_active /
-sparseoit_get_active; index lists must match exactly.  It also checks that a
-mask longer than the static maximum is rejected.  Run last: it must pass both
+sparseoit_get_active; index lists must match exactly, from the largest mask
+the scratch allows down to small ones.  It also checks that a mask longer than
+the static maximum is rejected.  Run last: it must pass both
 alone in a fresh process and after the rest of the suite.
 """
 import ctypes
@@ -42,7 +43,10 @@ def test_static_compaction_matches_set_active():
     __graft_entry__.build()
     lib = _lib.load()
     stream = torch.cuda.Stream()
-    cases = [(300_017, 0.05, 1), (70_001, 0.5, 2)]  # the second call is smaller: stale scratch must not leak
+    # largest first: the scratch left by a larger call must not leak into the smaller ones; the first
+    # two masks take more than one 1024-block chunk of the block-count scan (n > 4,194,304), the first
+    # is the largest mask the static scratch allows
+    cases = [(_lib.STATIC_MAX_SPLATS, 0.05, 3), (5_000_011, 0.2, 4), (300_017, 0.05, 1), (70_001, 0.5, 2)]
     for n, frac, seed in cases:
         m = scenes.random_active_mask(n, frac, seed)
         mask = torch.as_tensor(m, device="cuda")
