@@ -943,11 +943,14 @@ def main():
         out["sigma"] = torch.empty(1, dtype=torch.float32, device=dev)
         return out
 
-    def step(out):
-        r.forward(sp, [cam], [0], targets=[target], stream=stream, images=[img], loss=loss)
-        r.backward(sp, stream=stream, out=out)
+    def step(out, p):
+        r.forward(p, [cam], [0], targets=[target], stream=stream, images=[img], loss=loss)
+        r.backward(p, stream=stream, out=out)
 
     def timed(fraction, steps, warmup, profile=False):
+        """The step on the stage layout: the active rows are gathered once when the active set is set
+        (the active set, and so the gathered rows, stay fixed for the update interval of Sec. 4.1;
+        the gather is reported, not timed in the step)."""
         mask = make(fraction)
         with torch.cuda.stream(stream):
             r.set_active(mask, stream=stream)
@@ -957,20 +960,25 @@ def main():
             ev1.record(stream)
             stream.synchronize()
             commit_ms = ev0.elapsed_time(ev1)
+            ev0.record(stream)
+            p = r.gather_active(sp, stream=stream)
+            ev1.record(stream)
+            stream.synchronize()
+            gather_ms = ev0.elapsed_time(ev1)
             out = grads_for(r.n_active)
             # size the pair arena, count E and M (untimed)
             r.set_counting(True)
-            step(out)
+            step(out, p)
             r.status(stream)
             r.set_counting(False)
             M, E = r.last_counts(stream)
             for _ in range(warmup):
-                step(out)
+                step(out, p)
             stream.synchronize()
             # CUDA graph of one step (no host work between the kernels)
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=stream):
-                step(out)
+                step(out, p)
             for _ in range(2):
                 g.replay()
             stream.synchronize()
@@ -989,14 +997,14 @@ def main():
                 r.get_profile()
                 for _ in range(steps):
                     flush.zero_()
-                    step(out)
+                    step(out, p)
                 stream.synchronize()
                 prof = r.get_profile()
                 r.set_profiling(False)
             r.status(stream)
             del g
         return dict(ms=float(np.mean(times)), ms_min=float(np.min(times)), E=E, M=M, n_active=r.n_active,
-                    commit_recompute_ms=commit_ms, prof=prof, out=out, mask=mask)
+                    commit_recompute_ms=commit_ms, gather_ms=gather_ms, prof=prof, out=out, mask=mask, p=p)
 
     results = {}
     clock_path = os.path.join(_clock_dir(), f"clocks_rank{rank}.csv")
@@ -1043,43 +1051,54 @@ def main():
             stream.synchronize()
             set_active_ms, commit_inc_ms = a.elapsed_time(b), b.elapsed_time(c)
 
-        # end to end through the public API with host buffers: every step copies
-        # the full parameter arrays and the target from pinned host memory and
-        # reads back the compact gradients and the loss
-        host = {k: getattr(sp, k).cpu().pin_memory() for k in
-                ("means", "quats", "log_scales", "opacity_logits", "sh_color", "sh_weight")}
-        host_target = target.cpu().pin_memory()
-        with torch.cuda.stream(stream):
-            r.set_active(make(HEADLINE_FRACTION), stream=stream)
-            r.commit_frozen(sp, cam, 0, mode="recompute", stream=stream)
+        # end to end through the public API with host buffers, on the stage layout of the headline
+        # step: every step copies the active rows (the parameters the step trains) and the target from
+        # pinned host memory and reads back the compact gradients and the loss; the complement enters
+        # as its committed frozen sums, which stay on the device for the whole active stage
+        def e2e_time(params, host, host_target):
             out = grads_for(r.n_active)
             host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
             host_loss = torch.empty(1).pin_memory()
-            h2d = sum(v.numel() * v.element_size() for v in host.values()) + host_target.numel() * 4
-            d2h = sum(v.numel() * v.element_size() for v in out.values()) + 4
+            h2d_ = sum(v.numel() * v.element_size() for v in host.values()) + host_target.numel() * 4
+            d2h_ = sum(v.numel() * v.element_size() for v in out.values()) + 4
 
             def e2e_step():
                 for k, v in host.items():
-                    getattr(sp, k).copy_(v, non_blocking=True)
+                    getattr(params, k).copy_(v, non_blocking=True)
                 target.copy_(host_target, non_blocking=True)
-                step(out)
+                step(out, params)
                 for k, v in out.items():
                     host_out[k].copy_(v, non_blocking=True)
                 host_loss.copy_(loss, non_blocking=True)
 
-            for _ in range(args.warmup):
-                e2e_step()
-            stream.synchronize()
-            e_times = []
-            for _ in range(args.steps):
-                flush.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                e2e_step()
-                b.record(stream)
+            with torch.cuda.stream(stream):
+                for _ in range(args.warmup):
+                    e2e_step()
                 stream.synchronize()
-                e_times.append(a.elapsed_time(b))
-        e2e_ms = float(np.mean(e_times))
+                e_times = []
+                for _ in range(args.steps):
+                    flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    e2e_step()
+                    b.record(stream)
+                    stream.synchronize()
+                    e_times.append(a.elapsed_time(b))
+            return float(np.mean(e_times)), h2d_, d2h_
+
+        from paper_2605_13855_gb300.renderer import PARAM_NAMES
+        host_target = target.cpu().pin_memory()
+        with torch.cuda.stream(stream):
+            r.set_active(make(HEADLINE_FRACTION), stream=stream)
+            r.commit_frozen(sp, cam, 0, mode="recompute", stream=stream)
+            spa_e = r.gather_active(sp, stream=stream)
+            stream.synchronize()
+        host_a = {k: getattr(spa_e, k).cpu().pin_memory() for k in PARAM_NAMES}
+        e2e_ms, h2d, d2h = e2e_time(spa_e, host_a, host_target)
+        # the same with the whole parameter arrays (rows by splat, 1M splats) copied every step
+        host_full = {k: getattr(sp, k).cpu().pin_memory() for k in PARAM_NAMES}
+        e2e_full_ms, h2d_full, d2h_full = e2e_time(sp, host_full, host_target)
+        del host_full
         if ws > 1:
             e2e_ms, _ = reduce_over_ranks(e2e_ms, 0.0, device=dev)
 
@@ -1258,12 +1277,15 @@ def main():
                    "evals_per_step": head["E"], "pairs_per_step": head["M"],
                    "evals_tile_per_step": 256 * head["M"],
                    "l2": "flushed between timed steps (256 MiB write)", "timing": "CUDA graph replay, CUDA events",
+                   "layout": "stage layout: the active rows gathered once when the active set is set (fixed for "
+                             "the update interval, Sec. 4.1), the complement as committed frozen sums",
                    "parallelism": f"dp{ws} (one view per rank)"},
         "active_vs_full": None if full is None else {
             "ms_active": ms, "ms_full": full["ms"], "speedup": full["ms"] / ms,
             "evals_full": full["E"], "value_full": full["E"] / (full["ms"] * 1e-3)},
         "fractions": {str(f): {"ms": v["ms"], "ms_min": v["ms_min"], "evals": v["E"], "pairs": v["M"],
-                               "n_active": v["n_active"], "commit_recompute_ms": v["commit_recompute_ms"]}
+                               "n_active": v["n_active"], "commit_recompute_ms": v["commit_recompute_ms"],
+                               "gather_active_rows_ms": v["gather_ms"]}
                       for f, v in results.items()},
         "per_kernel_ms_full": None if full is None or not full["prof"] else {
             k: {"launches": n_, "avg_ms": t_ / max(1, n_)} for k, (n_, t_) in full["prof"].items()},
@@ -1278,7 +1300,11 @@ def main():
         "cpu_baseline": cpu,
         "e2e": None if e2e_ms is None else {
             "value": total_E / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
-            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "copies": "the active rows of every parameter array and the target in, the compact gradients and "
+                      "the loss out, each step (stage layout)",
+            "full_parameter_copy": {"value": total_E / (e2e_full_ms * 1e-3), "ms_per_step": e2e_full_ms,
+                                    "h2d_bytes_per_step": int(h2d_full), "d2h_bytes_per_step": int(d2h_full)}},
         "gpu_launches": gpu_launches,
         "clocks": clocks,
         "configs": configs,

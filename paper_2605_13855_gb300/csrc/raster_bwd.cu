@@ -102,10 +102,10 @@ __device__ __forceinline__ void load_tile_state(const ViewDesc &vd, int tx, int 
 // can reach the 0.99 clamp; without it min(a, 0.99) = a and the clamp
 // selects are left out (same results).
 template <bool kClamp>
-__device__ __forceinline__ void bwd_step(const BwdSplat &bs, float2 e1, float2 lg, bool in0, bool in1,
+__device__ __forceinline__ void bwd_step(const BwdSplat &bs, float2 e1, float2 nlg, bool in0, bool in1,
                                          const PixPair &ps, float2 &Rd, float2 &Re, BwdAcc &acc) {
     const float2 m1 = make_float2(-1.f, -1.f), one2 = make_float2(1.f, 1.f);
-    const float ar0 = fast_exp2(lg.x), ar1 = fast_exp2(lg.y);
+    const float ar0 = fast_exp2(-nlg.x), ar1 = fast_exp2(-nlg.y);
     float2 a, am;
     if (kClamp) {
         a = make_float2(in0 ? fminf(ar0, kAlphaMax) : 0.f, in1 ? fminf(ar1, kAlphaMax) : 0.f);
@@ -142,20 +142,20 @@ __device__ __forceinline__ void bwd_rows(const BwdSplat &bs, const TileState &S,
     const float2 zero2 = make_float2(0.f, 0.f);
     for (int ky = rlo; ky <= rhi; ++ky) {
         const RowTerms rt = row_terms(bs.A2dx0, bs.dy0, bs.rA2, bs.B2, bs.log2o, ky);
-        const float2 e10p = make_float2(rt.e10, rt.e10), lrp = make_float2(rt.lrow, rt.lrow);
+        const float2 e10p = make_float2(rt.e10, rt.e10), nlp = make_float2(rt.nlrow, rt.nlrow);
         float2 Rd = zero2, Re = zero2;
 #pragma unroll
         for (int m0 = 0; m0 < kTile / 2; m0 += 4) {
-            float2 e1[4], lg[4];
+            float2 e1[4], nlg[4];
             bool in[8];
             bool any = false;
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
                 const float kx = (float)(2 * (m0 + h));
                 e1[h] = __ffma2_rn(bs.A2p, make_float2(kx, kx + 1.f), e10p);
-                lg[h] = pair_lg2(e1[h], lrp);
-                in[2 * h] = !kTest || lg[h].x >= kMinLog2Alpha;
-                in[2 * h + 1] = !kTest || lg[h].y >= kMinLog2Alpha;
+                nlg[h] = pair_nlg2(e1[h], nlp);
+                in[2 * h] = !kTest || nlg[h].x <= kMaxNegLog2Alpha;
+                in[2 * h + 1] = !kTest || nlg[h].y <= kMaxNegLog2Alpha;
                 any = any || in[2 * h] || in[2 * h + 1];
             }
             if (!kTest || __any_sync(0xffffffffu, any)) {
@@ -163,8 +163,8 @@ __device__ __forceinline__ void bwd_rows(const BwdSplat &bs, const TileState &S,
                 for (int h = 0; h < 4; h += 2) {
                     PixPair p0, p1;
                     S.get2(ky, m0 + h, p0, p1);
-                    bwd_step<kClamp>(bs, e1[h], lg[h], in[2 * h], in[2 * h + 1], p0, Rd, Re, acc);
-                    bwd_step<kClamp>(bs, e1[h + 1], lg[h + 1], in[2 * h + 2], in[2 * h + 3], p1, Rd, Re, acc);
+                    bwd_step<kClamp>(bs, e1[h], nlg[h], in[2 * h], in[2 * h + 1], p0, Rd, Re, acc);
+                    bwd_step<kClamp>(bs, e1[h + 1], nlg[h + 1], in[2 * h + 2], in[2 * h + 3], p1, Rd, Re, acc);
                 }
             }
         }

@@ -82,15 +82,15 @@ __global__ void __launch_bounds__(kTilePix) raster_bwd_pixel_kernel(const __grid
             const float4 a0 = s0[j], a1 = s1[j];
             const RowTerms rt = row_terms(a0.x, a0.y, a0.z, a1.x, a1.z, ky);
             const float e1 = col_e1(a0.w, rt.e10, kx);
-            const float lg = pair_lg(e1, rt.lrow);
-            const bool in = lg >= kMinLog2Alpha;
+            const float nlg = pair_nlg(e1, rt.nlrow);
+            const bool in = nlg <= kMaxNegLog2Alpha;
             if (!__any_sync(0xffffffffu, in)) continue;
             float v10[10];
 #pragma unroll
             for (int k = 0; k < 10; ++k) v10[k] = 0.f;
             if (in) {
                 const float4 a2 = s2[j];
-                const float ar = fast_exp2(lg);
+                const float ar = fast_exp2(-nlg);
                 const float a = fminf(ar, kAlphaMax);
                 const float am = ar > kAlphaMax ? 0.f : a;
                 const float D = fmaf(Bg0, a2.x, fmaf(Bg1, a2.y, fmaf(Bg2, a2.z, nBgF)));

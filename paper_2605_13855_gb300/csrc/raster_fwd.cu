@@ -28,21 +28,21 @@ namespace soit {
 constexpr int kFwdBatch = 256;    // records staged per round
 constexpr int kFwdUnroll = 2;     // records per iteration of the accumulation loop
 
-// The strip's exponents log2 alpha_raw = lrow - e1^2, two pixels per f32x2
-// instruction where the strip has pairs (each component rounds like the
-// scalar FMA, so the decisions match the backward's).
+// The strip's negated exponents nlg = -log2 alpha_raw = e1^2 + nlrow, two
+// pixels per f32x2 instruction where the strip has pairs (each component
+// rounds like the scalar FMA, so the decisions match the backward's).
 template <int kStrip>
-__device__ __forceinline__ void strip_exponents(float A2, float e10, float lrow, int sx, float *lg) {
+__device__ __forceinline__ void strip_exponents(float A2, float e10, float nlrow, int sx, float *nlg) {
     if (kStrip == 1) {
-        lg[0] = pair_lg(col_e1(A2, e10, sx), lrow);
+        nlg[0] = pair_nlg(col_e1(A2, e10, sx), nlrow);
     } else {
-        const float2 A2p = make_float2(A2, A2), e10p = make_float2(e10, e10), lrp = make_float2(lrow, lrow);
+        const float2 A2p = make_float2(A2, A2), e10p = make_float2(e10, e10), nlp = make_float2(nlrow, nlrow);
 #pragma unroll
         for (int p = 0; p < kStrip; p += 2) {
             const float2 e1 = __ffma2_rn(A2p, make_float2((float)(sx + p), (float)(sx + p + 1)), e10p);
-            const float2 l = pair_lg2(e1, lrp);
-            lg[p] = l.x;
-            lg[p + 1] = l.y;
+            const float2 l = pair_nlg2(e1, nlp);
+            nlg[p] = l.x;
+            nlg[p + 1] = l.y;
         }
     }
 }
@@ -58,12 +58,12 @@ __device__ __forceinline__ void fwd_splat(const float4 *s0, const float4 *s1, co
     const float4 a0 = s0[j], a1 = s1[j], a2 = s2[j];
     const bool counted = kCount && j < kFwdBatch && in_view_row;  // the empty record counts nothing
     const RowTerms rt = row_terms(a0.x, a0.y, a0.z, a1.x, a1.z, ky);
-    float lg[kStrip];
-    strip_exponents<kStrip>(a0.w, rt.e10, rt.lrow, sx, lg);
+    float nlg[kStrip];
+    strip_exponents<kStrip>(a0.w, rt.e10, rt.nlrow, sx, nlg);
 #pragma unroll
     for (int p = 0; p < kStrip; ++p) {
-        if (!kTest || lg[p] >= kMinLog2Alpha) {
-            const float ar = fast_exp2(lg[p]);
+        if (!kTest || nlg[p] <= kMaxNegLog2Alpha) {
+            const float ar = fast_exp2(-nlg[p]);
             const float a = kClamp ? fminf(ar, kAlphaMax) : ar;
             const float2 aa = make_float2(a, a);
             b01[p] = __ffma2_rn(aa, make_float2(a2.x, a2.y), b01[p]);
