@@ -229,10 +229,12 @@ static int render_pass_bin(sparseoit_ctx *ctx, Batch &b, const sparseoit_splats 
     b.status = ctx->d_status;
     if (ctx->rec_cap < 3 * nrec || ctx->tile_cap < (int64_t)b.total_tiles + 1)
         return fail(ctx, SPARSEOIT_ERR_STATE, "batch workspace not sized");
-    // the tile counts and the scan scratch after them, zeroed together
-    CK(cudaMemsetAsync(ctx->d_tile_count, 0,
-                       (size_t)((char *)ctx->d_scan - (char *)ctx->d_tile_count) + scan_scratch_bytes(b.total_tiles), st),
-       "memset(tile counts, scan scratch)");
+    // the scan scratch and the batch's tile counters after it, zeroed together
+    CK(cudaMemsetAsync(ctx->d_scan, 0,
+                       (size_t)((char *)ctx->d_tile_count - (char *)ctx->d_scan) +
+                           (size_t)b.total_tiles * kTileCounterStride * sizeof(int),
+                       st),
+       "memset(scan scratch, tile counts)");
     const SplatPtrs sp = splat_ptrs(s);
     {
         ProfScope ps(ctx, "project", st);
@@ -271,7 +273,7 @@ static int ensure_batch_ws(sparseoit_ctx *ctx, int64_t nrec, int64_t tiles) {
         ctx->rec_cap = 3 * n;
     }
     if (ctx->tile_cap < tiles + 1) {
-        if (ctx->d_tile_count) cudaFree(ctx->d_tile_count);
+        if (ctx->d_scan) cudaFree(ctx->d_scan);
         if (ctx->d_offsets) cudaFree(ctx->d_offsets);
         if (ctx->d_cursor) cudaFree(ctx->d_cursor);
         if (ctx->d_order) cudaFree(ctx->d_order);
@@ -279,10 +281,11 @@ static int ensure_batch_ws(sparseoit_ctx *ctx, int64_t nrec, int64_t tiles) {
         ctx->d_scan = nullptr;
         ctx->tile_cap = 0;
         const int64_t n = tiles + 1;
-        // the tile counts with the scan scratch after them (256-byte aligned): one memset zeroes both
-        const size_t counts_bytes = ((size_t)n * sizeof(int) + 255) & ~(size_t)255;
-        CK(cudaMalloc((void **)&ctx->d_tile_count, counts_bytes + scan_scratch_bytes(n)), "cudaMalloc(tile counts)");
-        ctx->d_scan = (char *)ctx->d_tile_count + counts_bytes;
+        // the scan scratch with the tile counters after it (256-byte aligned): one memset zeroes both
+        const size_t scratch_bytes = (scan_scratch_bytes(n) + 255) & ~(size_t)255;
+        CK(cudaMalloc(&ctx->d_scan, scratch_bytes + (size_t)n * kTileCounterStride * sizeof(int)),
+           "cudaMalloc(tile counts)");
+        ctx->d_tile_count = reinterpret_cast<int *>((char *)ctx->d_scan + scratch_bytes);
         CK(cudaMalloc((void **)&ctx->d_offsets, (size_t)n * sizeof(int)), "cudaMalloc(tile offsets)");
         CK(cudaMalloc((void **)&ctx->d_cursor, (size_t)n * sizeof(int)), "cudaMalloc(tile cursors)");
         CK(cudaMalloc((void **)&ctx->d_order, (size_t)n * sizeof(int)), "cudaMalloc(tile order)");
@@ -424,7 +427,7 @@ int sparseoit_destroy(sparseoit_ctx *ctx) {
     for (float *p : ctx->d_frozen) if (p) cudaFree(p);
     for (float *p : ctx->d_state) if (p) cudaFree(p);
     void *bufs[] = {ctx->d_mask[0], ctx->d_mask[1], ctx->d_idx_active, ctx->d_idx_comp, ctx->d_idx_plus,
-                    ctx->d_idx_minus, ctx->d_blk, ctx->d_totals, ctx->d_rec, ctx->d_ext, ctx->d_tile_count,
+                    ctx->d_idx_minus, ctx->d_blk, ctx->d_totals, ctx->d_rec, ctx->d_ext, ctx->d_scan,
                     ctx->d_offsets, ctx->d_cursor, ctx->d_order, ctx->d_queue, ctx->d_pairs, ctx->d_sgrad, ctx->d_status,
                     ctx->d_npairs,
                     ctx->d_contrib, ctx->d_upd_image, ctx->d_upd_loss, ctx->d_ssim_abc, ctx->d_ssim_sums,

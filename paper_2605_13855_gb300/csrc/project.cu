@@ -149,8 +149,8 @@ __global__ void __launch_bounds__(256, 3) project_kernel(const __grid_constant__
                     for (int ty = ty0 + k; ty <= ty1; ty += G) {
                         int tx0, tx1;
                         if (!row_tiles(vd, mx, my, rr, B2, e, ty, tx0, tx1)) continue;
-                        int *row = tile_count + vd.tile_base + ty * vd.tiles_x;
-                        for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(row + tx, 1);
+                        int *row = tile_count + (int64_t)(vd.tile_base + ty * vd.tiles_x) * kTileCounterStride;
+                        for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(row + tx * kTileCounterStride, 1);
                     }
                 }
             }
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const int *__r
     int v[kScanPer], local = 0;
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) {
-        v[k] = base + k < total ? count[base + k] : 0;
+        v[k] = base + k < total ? count[(int64_t)(base + k) * kTileCounterStride] : 0;
         local += v[k];
         if (base + k < total) atomicAdd(&cls[load_class(v[k])], 1);
     }
@@ -337,7 +337,7 @@ __device__ __forceinline__ void place_tile_order(const int *__restrict__ count, 
     const int t = blk * kScanThreads + tid;
     int c = 0, slot = 0;
     if (t < total) {
-        c = load_class(count[t]);
+        c = load_class(count[(int64_t)t * kTileCounterStride]);
         slot = atomicAdd(&local[c], 1);
     }
     __syncthreads();
