@@ -8,7 +8,8 @@
 * batched: 3M splats, one view of each of the four resolutions of the
   16-view workload in one call, 5 % active, linear loss on a 96x96 window of
   each view (zero elsewhere on both sides); image on the windows and all
-  gradient groups compared.
+  gradient groups compared, with one raster block per tile and with the
+  persistent raster blocks that take the batch's tiles from a queue.
 """
 import numpy as np
 import pytest
@@ -104,19 +105,11 @@ def test_batched_3m_four_resolutions_windows():
         wins.append(win)
         gs.append(g)
     sp = SplatParams.from_numpy(scene)
-    r = Renderer(n, [(cm["width"], cm["height"]) for cm in cams], max_pairs=1 << 27)
-    r.set_active(torch.as_tensor(mask_np, device="cuda"))
+    # the oracle once: each view's window, the batch's gradient summed over its views
+    refs, total = [], None
     for v, cm in enumerate(cams):
-        r.commit_frozen(sp, cm, v, mode="recompute")
-    imgs, _ = r.forward(sp, cams, [0, 1, 2, 3])
-    grads = r.backward(sp, [torch.as_tensor(g, dtype=torch.float32, device="cuda") for g in gs])
-    r.status()
-    total = None
-    for v, cm in enumerate(cams):
-        x0, y0, x1, y1 = wins[v]
         ref = oracle.render(scene, cm, window=wins[v], amb_band=AMB_BAND)
-        e, frac = image_error(to_np(imgs[v])[y0:y1, x0:x1], ref["image"][y0:y1, x0:x1], ref["flip"][y0:y1, x0:x1])
-        assert e <= IMG_TOL and frac <= AMB_PIX_MAX, (v, e, frac)
+        refs.append(ref)
         rg = oracle_grads(scene, cm, ref["sums"], gs[v], active=act, window=wins[v])
         if total is None:
             total = rg
@@ -124,7 +117,24 @@ def test_batched_3m_four_resolutions_windows():
             for k in ("grads", "flip", "dsigma", "dsigma_scale", "dsigma_flip"):
                 total[k] = total[k] + rg[k]
             total["amb"] = total["amb"] | rg["amb"]
-    check_against_oracle(grads, total, np.where(act)[0])
+    # one block per tile (default) and persistent raster blocks over the tile queue
+    for opts in ({}, {"raster_persistent": 1}):
+        r = Renderer(n, [(cm["width"], cm["height"]) for cm in cams], max_pairs=1 << 27, **opts)
+        r.set_active(torch.as_tensor(mask_np, device="cuda"))
+        for v, cm in enumerate(cams):
+            r.commit_frozen(sp, cm, v, mode="recompute")
+        imgs, _ = r.forward(sp, cams, [0, 1, 2, 3])
+        grads = r.backward(sp, [torch.as_tensor(g, dtype=torch.float32, device="cuda") for g in gs])
+        r.status()
+        for v, cm in enumerate(cams):
+            x0, y0, x1, y1 = wins[v]
+            ref = refs[v]
+            e, frac = image_error(to_np(imgs[v])[y0:y1, x0:x1], ref["image"][y0:y1, x0:x1],
+                                  ref["flip"][y0:y1, x0:x1])
+            assert e <= IMG_TOL and frac <= AMB_PIX_MAX, (opts, v, e, frac)
+        check_against_oracle(grads, total, np.where(act)[0])
+        r.close()
+        del grads, imgs
 
 
 def test_unbounded_1m_dssim_loss_at_full_view():
