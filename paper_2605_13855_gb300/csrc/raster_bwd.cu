@@ -15,10 +15,13 @@
 // and, unless a is clamped at 0.99, dL/d(ln o) = a dL/da and
 // dL/ds = -ln2 a dL/da, chained to (mu'x, mu'y, r, A2, B2) below.
 //
-// The warps take groups of 32 of the tile's splats and walk the rows their
-// lanes' ellipses reach, eight pixels per warp vote (a group of four steps
-// runs when some lane has a contributing pixel in it; every lane evaluates
-// the same pixels, so the state loads are broadcasts).  By default each chunk
+// The warps take groups of 32 of the tile's splats and walk every pixel of
+// the rows their lanes' ellipses reach (every lane evaluates the same pixels,
+// so the state loads are broadcasts; a lane whose splat misses a pixel adds
+// exact zeros there).  A vote per group of pixels, skipping the groups that no
+// lane's ellipse reaches, saved under 1 % of the lane slots on the 1M-splat
+// workload and cost more than that in votes, branches and live predicates.
+// By default each chunk
 // of up to 1024 of the tile's pairs is first counting-sorted in shared memory
 // by where the splat starts in the tile (splats whose cutoff ellipse contains
 // the whole tile first, then by first row), and the warps take consecutive
@@ -97,8 +100,8 @@ __device__ __forceinline__ void load_tile_state(const ViewDesc &vd, int tx, int 
 }
 
 // One step of a lane: pixels (2m, 2m + 1) of a row against the lane's splat,
-// given their exponents and cutoff decisions; lanes without a contributing
-// pixel run it with a = 0, which adds exact zeros.  kClamp: some lane's splat
+// given their exponents and cutoff decisions; a pixel that does not
+// contribute runs it with a = 0, which adds exact zeros.  kClamp: some lane's splat
 // can reach the 0.99 clamp; without it min(a, 0.99) = a and the clamp
 // selects are left out (same results).
 template <bool kClamp>
@@ -133,10 +136,8 @@ __device__ __forceinline__ void bwd_step(const BwdSplat &bs, float2 e1, float2 n
 // Rows [rlo, rhi] of the tile.  kTest: test every pixel against the cutoff
 // (the pair contributes iff its exponent reaches -log2 255); without it every
 // pixel contributes (the warp's splats all contain the whole tile, or are
-// empty records whose alpha is 0).  A row is taken eight pixels at a time:
-// the four steps of a group run when some lane of the warp has a
-// contributing pixel in it (a warp vote, so the branch is uniform), and run
-// without branches between them, so that their chains interleave.
+// empty records whose alpha is 0).  The eight steps of a row run without
+// branches, so that their chains interleave.
 template <bool kTest, bool kClamp>
 __device__ __forceinline__ void bwd_rows(const BwdSplat &bs, const TileState &S, int rlo, int rhi, BwdAcc &acc) {
     const float2 zero2 = make_float2(0.f, 0.f);
@@ -148,7 +149,6 @@ __device__ __forceinline__ void bwd_rows(const BwdSplat &bs, const TileState &S,
         for (int m0 = 0; m0 < kTile / 2; m0 += 4) {
             float2 e1[4], nlg[4];
             bool in[8];
-            bool any = false;
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
                 const float kx = (float)(2 * (m0 + h));
@@ -156,16 +156,13 @@ __device__ __forceinline__ void bwd_rows(const BwdSplat &bs, const TileState &S,
                 nlg[h] = pair_nlg2(e1[h], nlp);
                 in[2 * h] = !kTest || nlg[h].x <= kMaxNegLog2Alpha;
                 in[2 * h + 1] = !kTest || nlg[h].y <= kMaxNegLog2Alpha;
-                any = any || in[2 * h] || in[2 * h + 1];
             }
-            if (!kTest || __any_sync(0xffffffffu, any)) {
 #pragma unroll
-                for (int h = 0; h < 4; h += 2) {
-                    PixPair p0, p1;
-                    S.get2(ky, m0 + h, p0, p1);
-                    bwd_step<kClamp>(bs, e1[h], nlg[h], in[2 * h], in[2 * h + 1], p0, Rd, Re, acc);
-                    bwd_step<kClamp>(bs, e1[h + 1], nlg[h + 1], in[2 * h + 2], in[2 * h + 3], p1, Rd, Re, acc);
-                }
+            for (int h = 0; h < 4; h += 2) {
+                PixPair p0, p1;
+                S.get2(ky, m0 + h, p0, p1);
+                bwd_step<kClamp>(bs, e1[h], nlg[h], in[2 * h], in[2 * h + 1], p0, Rd, Re, acc);
+                bwd_step<kClamp>(bs, e1[h + 1], nlg[h + 1], in[2 * h + 2], in[2 * h + 3], p1, Rd, Re, acc);
             }
         }
         const float rd = Rd.x + Rd.y, re = Re.x + Re.y;
@@ -251,7 +248,7 @@ constexpr int kBwdChunk = 1024;  // pairs sorted together (the heaviest tile of 
 // (the median tile holds ~110 splats at a 5 % active set) than eight, without stretching the
 // heaviest tiles into long serial chains as two do.
 constexpr int kBwdThreads = 128;
-constexpr int kBwdMinBlocks = 12 * 64 / kBwdThreads;  // <= 85 registers a thread
+constexpr int kBwdMinBlocks = 7;  // <= 73 registers a thread (6 blocks: 1.5 % slower; 8: the same as 7)
 
 // kSort: each chunk of up to kBwdChunk of the tile's pairs is counting-sorted in shared memory
 // by pair_key before the warps take groups of 32 from a shared counter (else the warps take the

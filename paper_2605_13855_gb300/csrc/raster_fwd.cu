@@ -7,7 +7,7 @@
 // tile-relative offsets, and sorted by warp ballots into one list of the
 // records whose cutoff ellipse contains the whole tile (evaluated without
 // cutoff tests) and, per warp, a list of the other records that reach its
-// rows; each warp walks its lists two records per branch-free iteration.  Every
+// rows; each warp walks its lists four records per branch-free iteration.  Every
 // pixel accumulates over the tile's splats P += a w c, Q += a w and
 // T *= (1 - a) (log T += log(1 - a) for the frozen sums), the sums taken in
 // 32-splat blocks added to the total, so that the FP32 rounding of sums over
@@ -26,7 +26,7 @@
 namespace soit {
 
 constexpr int kFwdBatch = 256;    // records staged per round
-constexpr int kFwdUnroll = 2;     // records per iteration of the accumulation loop
+constexpr int kFwdUnroll = 4;     // records per iteration of the accumulation loop
 
 // The strip's negated exponents nlg = -log2 alpha_raw = e1^2 + nlrow, two
 // pixels per f32x2 instruction where the strip has pairs (each component
@@ -199,44 +199,65 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
             if (tid < kWarps) wcnt[tid] = 0;
             __syncthreads();
             int may_clamp = 0;  // some staged splat can reach the 0.99 clamp
-            for (int k0 = 0; k0 < n; k0 += kFwdThreads) {  // uniform trip count: the lists use warp ballots
-                const int k = k0 + tid;
-                // staged: s0 = (A2 dx0, dy0, r A2, A2), s1 = (B2, 0, log2 o, yh),
-                //         s2 = (w c_r, w c_g, w c_b, w) (times the sign in sums mode)
-                bool ok = false, full = false;
-                float dy0 = 0.f, yh = -1.f;
-                if (k < n) {
-                    const uint32_t q = pairs[base + k];
-                    float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = make_float4(0.f, 0.f, -INFINITY, -1.f);
-                    float4 t2 = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (q < nrec) {  // never written by this call's scatter otherwise: contributes nothing
-                        const float4 a0 = rec[3 * (int64_t)q + 0];
-                        const float4 a1 = rec[3 * (int64_t)q + 1];
-                        const float4 a2 = rec[3 * (int64_t)q + 2];
-                        const SplatConsts c = splat_consts(ox, oy, a0.x, a0.y, a0.z, a0.w);
-                        t0 = make_float4(c.A2dx0, c.dy0, c.rA2, a0.w);
-                        t1 = make_float4(a1.x, 0.f, a1.y, a1.w);
-                        ok = true;
-                        // the whole tile inside the cutoff ellipse (its four corner pixels are, by a margin)
-                        full = tile_inside(c, a0.w, a1.x, a1.y);
-                        dy0 = c.dy0;
-                        yh = a1.w;
-                        may_clamp |= a1.y > kNoClampLog2 ? 1 : 0;
-                        const float ws = kMode == kRasterSums ? a1.z * a2.w : a1.z;
-                        t2 = make_float4(ws * a2.x, ws * a2.y, ws * a2.z, ws);
-                        if (kMode == kRasterSums) ssign[k] = a2.w;
-                    }
-                    s0[k] = t0;
-                    s1[k] = t1;
-                    s2[k] = t2;
+            for (int k0 = 0; k0 < n; k0 += 2 * kFwdThreads) {  // uniform trip count: the lists use warp ballots
+                // two records a thread: both pair indices, then both records, are loaded before use
+                uint32_t qv[2];
+                float4 r0[2], r1[2], r2[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int k = k0 + u * kFwdThreads + tid;
+                    qv[u] = k < n ? pairs[base + k] : 0xffffffffu;
                 }
-                list_append(ok && full, k, &fcnt, flist);
-    #pragma unroll
-                for (int w = 0; w < kWarps; ++w) {
-                    // the ellipse's rows |dy0 + ky| <= yh reach rows [w R, w R + R - 1] of the tile
-                    const float dlo = dy0 + (float)(w * kRowsPerWarp);
-                    const bool hit = ok && !full && !(dlo > yh || dlo + (float)(kRowsPerWarp - 1) < -yh);
-                    list_append(hit, k, &wcnt[w], wlist[w]);
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    r0[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    r1[u] = r2[u] = r0[u];
+                    if (qv[u] < nrec) {
+                        r0[u] = rec[3 * (int64_t)qv[u] + 0];
+                        r1[u] = rec[3 * (int64_t)qv[u] + 1];
+                        r2[u] = rec[3 * (int64_t)qv[u] + 2];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int k = k0 + u * kFwdThreads + tid;
+                    // staged: s0 = (A2 dx0, dy0, r A2, A2), s1 = (B2, 0, log2 o, yh),
+                    //         s2 = (w c_r, w c_g, w c_b, w) (times the sign in sums mode)
+                    bool ok = false, full = false;
+                    float dy0 = 0.f, yh = -1.f;
+                    if (k < n) {
+                        const uint32_t q = qv[u];
+                        float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = make_float4(0.f, 0.f, -INFINITY, -1.f);
+                        float4 t2 = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (q < nrec) {  // never written by this call's scatter otherwise: contributes nothing
+                            const float4 a0 = r0[u];
+                            const float4 a1 = r1[u];
+                            const float4 a2 = r2[u];
+                            const SplatConsts c = splat_consts(ox, oy, a0.x, a0.y, a0.z, a0.w);
+                            t0 = make_float4(c.A2dx0, c.dy0, c.rA2, a0.w);
+                            t1 = make_float4(a1.x, 0.f, a1.y, a1.w);
+                            ok = true;
+                            // the whole tile inside the cutoff ellipse (its four corner pixels are, by a margin)
+                            full = tile_inside(c, a0.w, a1.x, a1.y);
+                            dy0 = c.dy0;
+                            yh = a1.w;
+                            may_clamp |= a1.y > kNoClampLog2 ? 1 : 0;
+                            const float ws = kMode == kRasterSums ? a1.z * a2.w : a1.z;
+                            t2 = make_float4(ws * a2.x, ws * a2.y, ws * a2.z, ws);
+                            if (kMode == kRasterSums) ssign[k] = a2.w;
+                        }
+                        s0[k] = t0;
+                        s1[k] = t1;
+                        s2[k] = t2;
+                    }
+                    list_append(ok && full, k, &fcnt, flist);
+#pragma unroll
+                    for (int w = 0; w < kWarps; ++w) {
+                        // the ellipse's rows |dy0 + ky| <= yh reach rows [w R, w R + R - 1] of the tile
+                        const float dlo = dy0 + (float)(w * kRowsPerWarp);
+                        const bool hit = ok && !full && !(dlo > yh || dlo + (float)(kRowsPerWarp - 1) < -yh);
+                        list_append(hit, k, &wcnt[w], wlist[w]);
+                    }
                 }
             }
             const bool clamp = __syncthreads_or(may_clamp) != 0;
