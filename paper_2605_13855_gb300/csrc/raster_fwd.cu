@@ -142,6 +142,8 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
     __shared__ uint16_t flist[kFwdBatch], wlist[kWarps][kFwdBatch];
     __shared__ int fcnt, wcnt[kWarps];
     __shared__ float red[kFwdThreads / 32];
+    // the tile's sums (P_r, P_g, P_b, Q, T or log T) by pixel, for the epilogue's row-contiguous mapping
+    __shared__ float psum[5][kTilePix];
     __shared__ unsigned red_n[kFwdThreads / 32];
 
     __shared__ int item_s;
@@ -275,30 +277,43 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
             }
         }
 
+        // the sums to shared memory, then the epilogue with a thread per pixel and consecutive
+        // threads on consecutive pixels of a row: each load and store of a plane covers two
+        // contiguous row segments per warp (a thread's own strip would scatter them over 8 rows)
+#pragma unroll
+        for (int p = 0; p < kStrip; ++p) {
+            const int i = ky * kTile + sx + p;
+            psum[0][i] = P01[p].x;
+            psum[1][i] = P01[p].y;
+            psum[2][i] = P2Q[p].x;
+            psum[3][i] = P2Q[p].y;
+            psum[4][i] = T[p];
+        }
+        __syncthreads();
         const int64_t HW = (int64_t)vd.W * vd.H;
-        const int y = ty * kTile + ky;
         float my_loss = 0.f;
         const float inv3hw = 1.f / (3.f * (float)HW);
     #pragma unroll
-        for (int p = 0; p < kStrip; ++p) {
-            const int x = tx * kTile + sx + p;
+        for (int i = tid; i < kTilePix; i += kFwdThreads) {
+            const int x = tx * kTile + (i & (kTile - 1)), y = ty * kTile + i / kTile;
             if (x >= vd.W || y >= vd.H) continue;
             const int64_t pix = (int64_t)y * vd.W + x;
+            const float p0 = psum[0][i], p1 = psum[1][i], p2 = psum[2][i], pq = psum[3][i], pt = psum[4][i];
             if (kMode == kRasterSums) {
                 float *fz = vd.frozen;
-                fz[pix] += P01[p].x;
-                fz[HW + pix] += P01[p].y;
-                fz[2 * HW + pix] += P2Q[p].x;
-                fz[3 * HW + pix] += P2Q[p].y;
-                fz[4 * HW + pix] += T[p];
+                fz[pix] += p0;
+                fz[HW + pix] += p1;
+                fz[2 * HW + pix] += p2;
+                fz[3 * HW + pix] += pq;
+                fz[4 * HW + pix] += pt;
             } else {
                 // the frozen complement's sums (none when the whole set is rendered)
                 const float *fz = vd.frozen;
                 const float f0 = fz ? fz[pix] : 0.f, f1 = fz ? fz[HW + pix] : 0.f, f2 = fz ? fz[2 * HW + pix] : 0.f;
                 const float fq = fz ? fz[3 * HW + pix] : 0.f;
-                const float Pt0 = P01[p].x + f0, Pt1 = P01[p].y + f1, Pt2 = P2Q[p].x + f2;
-                const float Qt = P2Q[p].y + fq;
-                const float Tt = fz ? T[p] * expf(fz[4 * HW + pix]) : T[p];
+                const float Pt0 = p0 + f0, Pt1 = p1 + f1, Pt2 = p2 + f2;
+                const float Qt = pq + fq;
+                const float Tt = fz ? pt * expf(fz[4 * HW + pix]) : pt;
                 const float invQ = Qt > 0.f ? 1.f / Qt : 0.f;
                 const float F0 = Pt0 * invQ, F1 = Pt1 * invQ, F2 = Pt2 * invQ;
                 const float omT = 1.f - Tt;
