@@ -3,18 +3,72 @@
 // parameters: Eq. 6 (EWA projection), Eq. 2 (covariance from quaternion and
 // scales), Eq. 4 (SH colour), Eq. 1 (OIT weight and sigma), Sec. 3.1
 // (opacity = sigmoid(logit)).  One thread per active splat; the views of the
-// batch are summed in registers and every gradient row is written once.
+// batch are summed in registers and every gradient row is written once.  The
+// block's SH coefficient rows (48 + 16 values a splat) pass through shared
+// memory: the block copies them in, and its gradient rows out, with
+// coalesced 16-byte accesses, and each thread reads and writes its own
+// (padded) row there; per-thread global accesses to 192- and 64-byte rows
+// would touch a different cache line in every lane of each warp access.
 #include "common.cuh"
 #include "launch.h"
 
 namespace soit {
 
+constexpr int kChainThreads = 128;
+constexpr int kRowC4 = 13;  // float4 per staged colour row (12 + 1: consecutive rows land on different banks)
+constexpr int kRowW4 = 5;   // float4 per staged weight row (4 + 1)
+
+// Row r of the block (parameter row pi) into the staging rows, as FP32.
 template <typename ShT>
-__global__ void __launch_bounds__(128, 3) project_bwd_kernel(const __grid_constant__ Batch b, SplatPtrs sp,
+__device__ __forceinline__ void stage_sh_rows(const SplatPtrs &sp, const int *list, int r0, int nb, float4 *shc,
+                                              float4 *shw) {
+    constexpr int kC16 = 48 * (int)sizeof(ShT) / 16, kW16 = 16 * (int)sizeof(ShT) / 16;  // 16-byte chunks a row
+    constexpr int kPer = 16 / (int)sizeof(ShT);                                           // values a chunk
+    for (int idx = threadIdx.x; idx < nb * (kC16 + kW16); idx += kChainThreads) {
+        const int row = idx / (kC16 + kW16), part = idx - row * (kC16 + kW16);
+        const int pi = sp.active_rows ? r0 + row : list[r0 + row];
+        const bool colour = part < kC16;
+        const int c = colour ? part : part - kC16;
+        const ShT *src = reinterpret_cast<const ShT *>(colour ? sp.sh_color : sp.sh_weight) +
+                         (int64_t)pi * (colour ? 48 : 16) + c * kPer;
+        float *dst = reinterpret_cast<float *>(colour ? shc + row * kRowC4 : shw + row * kRowW4) + c * kPer;
+        if (sizeof(ShT) == 4) {
+            *reinterpret_cast<float4 *>(dst) = __ldg(reinterpret_cast<const float4 *>(src));
+        } else {
+            const uint4 raw = __ldg(reinterpret_cast<const uint4 *>(src));
+            const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {  // bf16 pair -> two floats (bf16 is the top half of an fp32)
+                dst[2 * k] = __uint_as_float(w[k] << 16);
+                dst[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+            }
+        }
+    }
+}
+
+// SH coefficients c0 .. c0 + 3 of the thread's staged rows (colour layout (r0 g0 b0 r1) (g1 b1 r2 g2) ...).
+__device__ __forceinline__ void staged_sh_run(const float4 *hc, const float4 *hw, int c0, float h0[4], float h1[4],
+                                              float h2[4], float hv[4]) {
+    const float4 a = hc[3 * c0 / 4], b = hc[3 * c0 / 4 + 1], c = hc[3 * c0 / 4 + 2];
+    h0[0] = a.x; h1[0] = a.y; h2[0] = a.z;
+    h0[1] = a.w; h1[1] = b.x; h2[1] = b.y;
+    h0[2] = b.z; h1[2] = b.w; h2[2] = c.x;
+    h0[3] = c.y; h1[3] = c.z; h2[3] = c.w;
+    const float4 w = hw[c0 / 4];
+    hv[0] = w.x; hv[1] = w.y; hv[2] = w.z; hv[3] = w.w;
+}
+
+template <typename ShT>
+__global__ void __launch_bounds__(kChainThreads, 3) project_bwd_kernel(const __grid_constant__ Batch b, SplatPtrs sp,
                                                           const int *__restrict__ list, int n,
                                                           const float4 *__restrict__ sgrad, GradPtrs out) {
     __shared__ float red[4];
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ float4 shc[kChainThreads * kRowC4], shw[kChainThreads * kRowW4];
+    const int r0 = blockIdx.x * kChainThreads, nb = min(kChainThreads, n - r0);
+    stage_sh_rows<ShT>(sp, list, r0, nb, shc, shw);
+    __syncthreads();
+    const int r = r0 + threadIdx.x;
+    float4 *myc = shc + threadIdx.x * kRowC4, *myw = shw + threadIdx.x * kRowW4;
     float gsig_local = 0.f;
     if (r < n) {
         const int i = list[r];
@@ -26,8 +80,6 @@ __global__ void __launch_bounds__(128, 3) project_bwd_kernel(const __grid_consta
         for (int k = 0; k < 3; ++k) ls[k] = __ldg(sp.log_scales + 3 * (int64_t)pi + k);
         const float ol = __ldg(sp.opacity_logits + pi);
         const float o = 1.f / (1.f + expf(-ol));
-        const ShT *hc = reinterpret_cast<const ShT *>(sp.sh_color) + 48 * (int64_t)pi;
-        const ShT *hw = reinterpret_cast<const ShT *>(sp.sh_weight) + 16 * (int64_t)pi;
 
         float g_mu[3] = {0.f, 0.f, 0.f}, g_q[4] = {0.f, 0.f, 0.f, 0.f}, g_ls[3] = {0.f, 0.f, 0.f}, g_ol = 0.f;
         float g_h[48], g_hw[16];
@@ -108,7 +160,7 @@ __global__ void __launch_bounds__(128, 3) project_bwd_kernel(const __grid_consta
 #pragma unroll
             for (int q4 = 0; q4 < 4; ++q4) {  // coefficients 4 q4 .. 4 q4 + 3, vector loads
                 float h0[4], h1[4], h2[4], hv[4];
-                load_sh_run<ShT, 4>(hc, hw, 4 * q4, h0, h1, h2, hv);
+                staged_sh_run(myc, myw, 4 * q4, h0, h1, h2, hv);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int k = 4 * q4 + j;
@@ -134,7 +186,7 @@ __global__ void __launch_bounds__(128, 3) project_bwd_kernel(const __grid_consta
 #pragma unroll
             for (int q4 = 0; q4 < 4; ++q4) {
                 float h0[4], h1[4], h2[4], hv[4];
-                load_sh_run<ShT, 4>(hc, hw, 4 * q4, h0, h1, h2, hv);
+                staged_sh_run(myc, myw, 4 * q4, h0, h1, h2, hv);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int k = 4 * q4 + j;
@@ -172,33 +224,36 @@ __global__ void __launch_bounds__(128, 3) project_bwd_kernel(const __grid_consta
         }
         const int64_t row = out.rows_by_splat ? (int64_t)i : (int64_t)r;
         float4 *oq = reinterpret_cast<float4 *>(out.quats) + row;
-        float4 *oh = reinterpret_cast<float4 *>(out.sh_color + 48 * row);
-        float4 *ow = reinterpret_cast<float4 *>(out.sh_weight + 16 * row);
         if (out.accumulate) {  // add to the caller's running sums (several backward calls)
             for (int k = 0; k < 3; ++k) g_mu[k] += out.means[3 * row + k];
             const float4 pq = *oq;
             g_q[0] += pq.x; g_q[1] += pq.y; g_q[2] += pq.z; g_q[3] += pq.w;
             for (int k = 0; k < 3; ++k) g_ls[k] += out.log_scales[3 * row + k];
             g_ol += out.opacity_logits[row];
-#pragma unroll
-            for (int k = 0; k < 12; ++k) {
-                const float4 h = oh[k];
-                g_h[4 * k] += h.x; g_h[4 * k + 1] += h.y; g_h[4 * k + 2] += h.z; g_h[4 * k + 3] += h.w;
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float4 h = ow[k];
-                g_hw[4 * k] += h.x; g_hw[4 * k + 1] += h.y; g_hw[4 * k + 2] += h.z; g_hw[4 * k + 3] += h.w;
-            }
         }
         for (int k = 0; k < 3; ++k) out.means[3 * row + k] = g_mu[k];
         *oq = make_float4(g_q[0], g_q[1], g_q[2], g_q[3]);
         for (int k = 0; k < 3; ++k) out.log_scales[3 * row + k] = g_ls[k];
         out.opacity_logits[row] = g_ol;
+        // the SH gradient rows into the thread's own staging rows (its parameter reads are done)
 #pragma unroll
-        for (int k = 0; k < 12; ++k) oh[k] = make_float4(g_h[4 * k], g_h[4 * k + 1], g_h[4 * k + 2], g_h[4 * k + 3]);
+        for (int k = 0; k < 12; ++k) myc[k] = make_float4(g_h[4 * k], g_h[4 * k + 1], g_h[4 * k + 2], g_h[4 * k + 3]);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) ow[k] = make_float4(g_hw[4 * k], g_hw[4 * k + 1], g_hw[4 * k + 2], g_hw[4 * k + 3]);
+        for (int k = 0; k < 4; ++k) myw[k] = make_float4(g_hw[4 * k], g_hw[4 * k + 1], g_hw[4 * k + 2], g_hw[4 * k + 3]);
+    }
+    __syncthreads();
+    // the block's SH gradient rows out, coalesced (added to the running sums when accumulating)
+    for (int idx = threadIdx.x; idx < nb * 16; idx += kChainThreads) {
+        const int row = idx >> 4, part = idx & 15;
+        const int64_t orow = out.rows_by_splat ? (int64_t)list[r0 + row] : (int64_t)(r0 + row);
+        float4 *dst = part < 12 ? reinterpret_cast<float4 *>(out.sh_color + 48 * orow) + part
+                                : reinterpret_cast<float4 *>(out.sh_weight + 16 * orow) + (part - 12);
+        float4 v = part < 12 ? shc[row * kRowC4 + part] : shw[row * kRowW4 + part - 12];
+        if (out.accumulate) {
+            const float4 o4 = *dst;
+            v.x += o4.x; v.y += o4.y; v.z += o4.z; v.w += o4.w;
+        }
+        *dst = v;
     }
     // dL/dsigma: block reduction, one atomic per block
 #pragma unroll
@@ -214,11 +269,11 @@ __global__ void __launch_bounds__(128, 3) project_bwd_kernel(const __grid_consta
 int launch_project_bwd(const Batch &b, const SplatPtrs &sp, bool bf16, const int *list, int n, const float4 *sgrad,
                        GradPtrs out, cudaStream_t st) {
     if (n == 0) return 0;
-    const int grid = (n + 127) / 128;
+    const int grid = (n + kChainThreads - 1) / kChainThreads;
     if (bf16)
-        project_bwd_kernel<__nv_bfloat16><<<grid, 128, 0, st>>>(b, sp, list, n, sgrad, out);
+        project_bwd_kernel<__nv_bfloat16><<<grid, kChainThreads, 0, st>>>(b, sp, list, n, sgrad, out);
     else
-        project_bwd_kernel<float><<<grid, 128, 0, st>>>(b, sp, list, n, sgrad, out);
+        project_bwd_kernel<float><<<grid, kChainThreads, 0, st>>>(b, sp, list, n, sgrad, out);
     return 0;
 }
 
