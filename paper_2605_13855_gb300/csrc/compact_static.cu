@@ -66,14 +66,36 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *warp_tot, int *t
     return warp_tot[warp] + incl - v;
 }
 
+// Bit k set iff mask[i0 + k] != 0 (k < kPer, i0 + k < n): one 16-byte load when the run is aligned
+// and whole, else byte loads.  Per 32-bit word x, ((x & 0x7f7f7f7f) + 0x7f7f7f7f) | x has the top
+// bit of each byte set iff that byte is non-zero (no carry crosses a byte), and multiplying the
+// four top bits by 1 + 2^7 + 2^14 + 2^21 gathers them into bits 28..31 in byte order.
+__device__ __forceinline__ unsigned mask_bits16(const uint8_t *__restrict__ mask, int64_t i0, int64_t n) {
+    static_assert(kPer == 16, "one uint4 a thread");
+    const uint8_t *p = mask + i0;
+    if (i0 + kPer <= n && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        unsigned bits = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t t = (((w[k] & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w[k]) & 0x80808080u;
+            bits |= ((t * 0x00204081u) >> 28) << (4 * k);
+        }
+        return bits;
+    }
+    unsigned bits = 0;
+    for (int k = 0; k < kPer; ++k)
+        if (i0 + k < n && p[k] != 0) bits |= 1u << k;
+    return bits;
+}
+
 __global__ void __launch_bounds__(kThreads) static_count_kernel(const uint8_t *__restrict__ mask, int64_t n,
                                                                 int *__restrict__ scratch) {
     __shared__ int wt[kThreads / 32];
     __shared__ int tot;
     const int64_t i0 = (int64_t)blockIdx.x * kBlockElems + (int64_t)threadIdx.x * kPer;
-    int c = 0;
-    for (int k = 0; k < kPer; ++k)
-        if (i0 + k < n && mask[i0 + k] != 0) ++c;
+    const int c = __popc(mask_bits16(mask, i0, n));
     block_exclusive_scan(c, wt, &tot);
     if (threadIdx.x == 0) scratch[blockIdx.x] = tot;
 }
@@ -123,11 +145,8 @@ __global__ void __launch_bounds__(kThreads) static_write_kernel(const uint8_t *_
     __shared__ int wt[kThreads / 32];
     __shared__ int tot;
     const int64_t i0 = (int64_t)blockIdx.x * kBlockElems + (int64_t)threadIdx.x * kPer;
-    unsigned bits = 0;
-    int c = 0;
-    for (int k = 0; k < kPer; ++k)
-        if (i0 + k < n && mask[i0 + k] != 0) { bits |= 1u << k; ++c; }
-    int pos = scratch[blockIdx.x] + block_exclusive_scan(c, wt, &tot);
+    const unsigned bits = mask_bits16(mask, i0, n);
+    int pos = scratch[blockIdx.x] + block_exclusive_scan(__popc(bits), wt, &tot);
     for (int k = 0; k < kPer; ++k)
         if (bits & (1u << k)) idx[pos++] = (int32_t)(i0 + k);
 }
