@@ -44,14 +44,16 @@ namespace soit {
 //   dL/ds = -ln2 da.  Summing K = -2 ln2 times
 //     Se = sum da e1, Sey = sum da e1 dy, See = sum da e1^2,
 //     Sdy = sum da dy, Sdyy = sum da dy^2
-// (the dy sums taken per tile row, where dy is constant) gives
+// (the dy sums taken per tile row, where dy is constant; per row See comes
+// from sum da nlg - nlrow sum da, since the pixel's rounded exponent is
+// nlg = e1^2 + nlrow, which saves the product da e1 per pixel) gives
 //   dL/dmu'x = -K A2 Se,  dL/dmu'y = K (A2 r Se - B2^2 Sdy),
 //   dL/dr = -K A2 Sey,    dL/dA2 = K See / A2,  dL/dB2 = K B2 Sdyy.
 
 // Per-lane accumulators of one splat over the tile (see the sums above).
 struct BwdAcc {
-    float2 See, gw, gc0, gc1, gc2;
-    float Se, Sey, Sd, Sdy, Sdyy;
+    float2 gw, gc0, gc1, gc2;
+    float See, Se, Sey, Sd, Sdy, Sdyy;
 };
 struct BwdSplat {
     float2 A2p, wp, c0p, c1p, c2p;
@@ -106,7 +108,7 @@ __device__ __forceinline__ void load_tile_state(const ViewDesc &vd, int tx, int 
 // selects are left out (same results).
 template <bool kClamp>
 __device__ __forceinline__ void bwd_step(const BwdSplat &bs, float2 e1, float2 nlg, bool in0, bool in1,
-                                         const PixPair &ps, float2 &Rd, float2 &Re, BwdAcc &acc) {
+                                         const PixPair &ps, float2 &Rd, float2 &Re, float2 &Rn, BwdAcc &acc) {
     const float2 m1 = make_float2(-1.f, -1.f), one2 = make_float2(1.f, 1.f);
     const float ar0 = fast_exp2(-nlg.x), ar1 = fast_exp2(-nlg.y);
     float2 a, am;
@@ -128,9 +130,8 @@ __device__ __forceinline__ void bwd_step(const BwdSplat &bs, float2 e1, float2 n
     acc.gc2 = __ffma2_rn(a, ps.b2, acc.gc2);
     const float2 da = __fmul2_rn(dLda, am);
     Rd = __fadd2_rn(Rd, da);
-    const float2 qd = __fmul2_rn(da, e1);
-    Re = __fadd2_rn(Re, qd);
-    acc.See = __ffma2_rn(qd, e1, acc.See);
+    Re = __ffma2_rn(da, e1, Re);
+    Rn = __ffma2_rn(da, nlg, Rn);  // e1^2 = nlg - nlrow: the row adds Rn - nlrow Rd to See
 }
 
 // Rows [rlo, rhi] of the tile.  kTest: test every pixel against the cutoff
@@ -144,7 +145,7 @@ __device__ __forceinline__ void bwd_rows(const BwdSplat &bs, const TileState &S,
     for (int ky = rlo; ky <= rhi; ++ky) {
         const RowTerms rt = row_terms(bs.A2dx0, bs.dy0, bs.rA2, bs.B2, bs.log2o, ky);
         const float2 e10p = make_float2(rt.e10, rt.e10), nlp = make_float2(rt.nlrow, rt.nlrow);
-        float2 Rd = zero2, Re = zero2;
+        float2 Rd = zero2, Re = zero2, Rn = zero2;
 #pragma unroll
         for (int m0 = 0; m0 < kTile / 2; m0 += 4) {
             float2 e1[4], nlg[4];
@@ -161,11 +162,12 @@ __device__ __forceinline__ void bwd_rows(const BwdSplat &bs, const TileState &S,
             for (int h = 0; h < 4; h += 2) {
                 PixPair p0, p1;
                 S.get2(ky, m0 + h, p0, p1);
-                bwd_step<kClamp>(bs, e1[h], nlg[h], in[2 * h], in[2 * h + 1], p0, Rd, Re, acc);
-                bwd_step<kClamp>(bs, e1[h + 1], nlg[h + 1], in[2 * h + 2], in[2 * h + 3], p1, Rd, Re, acc);
+                bwd_step<kClamp>(bs, e1[h], nlg[h], in[2 * h], in[2 * h + 1], p0, Rd, Re, Rn, acc);
+                bwd_step<kClamp>(bs, e1[h + 1], nlg[h + 1], in[2 * h + 2], in[2 * h + 3], p1, Rd, Re, Rn, acc);
             }
         }
-        const float rd = Rd.x + Rd.y, re = Re.x + Re.y;
+        const float rd = Rd.x + Rd.y, re = Re.x + Re.y, rn = Rn.x + Rn.y;
+        acc.See += fmaf(-rt.nlrow, rd, rn);
         acc.Sd += rd;
         acc.Sdy = fmaf(rd, rt.dy, acc.Sdy);
         acc.Sdyy = fmaf(rd, rt.dy * rt.dy, acc.Sdyy);
@@ -199,8 +201,8 @@ __device__ __forceinline__ void bwd_group(const float4 *__restrict__ rec, uint32
 
     const float2 zero2 = make_float2(0.f, 0.f);
     BwdAcc acc;
-    acc.See = acc.gw = acc.gc0 = acc.gc1 = acc.gc2 = zero2;
-    acc.Se = acc.Sey = acc.Sd = acc.Sdy = acc.Sdyy = 0.f;
+    acc.gw = acc.gc0 = acc.gc1 = acc.gc2 = zero2;
+    acc.See = acc.Se = acc.Sey = acc.Sd = acc.Sdy = acc.Sdyy = 0.f;
     const BwdSplat bs{make_float2(A2, A2), make_float2(w, w), make_float2(a2.x, a2.x), make_float2(a2.y, a2.y),
                       make_float2(a2.z, a2.z), sc.A2dx0, sc.dy0, sc.rA2, B2, log2o};
     // a splat with log2 o <= kNoClampLog2 never reaches the 0.99 clamp
@@ -218,7 +220,7 @@ __device__ __forceinline__ void bwd_group(const float4 *__restrict__ rec, uint32
     }
     if (valid) {
         const float K = -2.f * kLn2;
-        const float See1 = acc.See.x + acc.See.y;
+        const float See1 = acc.See;
         const float g_mx = -K * A2 * acc.Se;
         const float g_my = K * (A2 * rr * acc.Se - B2 * B2 * acc.Sdy);
         const float g_r = -K * A2 * acc.Sey;
