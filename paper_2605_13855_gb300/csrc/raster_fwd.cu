@@ -3,7 +3,7 @@
 // One block per 16x16 tile; each thread owns a 1xS strip of pixels of one
 // row (S = 1, 2 or 4, a launch parameter; the exponent of each pixel of the
 // strip costs two FMAs), each warp owns 2S rows.  The tile's records are
-// staged through shared memory 256 at a time, already shifted to
+// staged through shared memory 128 at a time, already shifted to
 // tile-relative offsets, and sorted by warp ballots into one list of the
 // records whose cutoff ellipse contains the whole tile (evaluated without
 // cutoff tests) and, per warp, a list of the other records that reach its
@@ -25,7 +25,10 @@
 
 namespace soit {
 
-constexpr int kFwdBatch = 256;    // records staged per round
+// Records staged per round.  128 keeps a block's shared memory at 12 KB, so that with the strip
+// of 4 pixels 12 blocks (24 warps, 80 registers a thread) fit an SM; 256 records at 19 KB allowed
+// 9 (106 registers) and measured 5 % slower on the 1M-splat / 5 % workload.
+constexpr int kFwdBatch = 128;
 constexpr int kFwdUnroll = 4;     // records per iteration of the accumulation loop
 
 // The strip's negated exponents nlg = -log2 alpha_raw = e1^2 + nlrow, two
@@ -122,8 +125,10 @@ __device__ __forceinline__ void list_append(bool flag, int k, int *cnt, uint16_t
     if (flag) list[wb + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)k;
 }
 
+// Blocks per SM asked of the compiler: 12 for the 4-pixel strip (at most 80 registers; 14 blocks
+// at 72 registers and 16 at 64 spill and measured slower).
 template <int kMode, bool kCount, int kStrip>
-__global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip == 2 ? 4 : 8)) raster_fwd_kernel(const __grid_constant__ Batch b,
+__global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip == 2 ? 4 : 12)) raster_fwd_kernel(const __grid_constant__ Batch b,
                                                                  const float4 *__restrict__ rec,
                                                                  const int *__restrict__ offsets,
                                                                  const uint32_t *__restrict__ pairs, int64_t cap,
