@@ -81,9 +81,9 @@ __device__ __forceinline__ void fwd_splat(const float4 *s0, const float4 *s1, co
 }
 
 // A list of staged records (indices into the staged arrays) into the
-// thread's strip, kFwdUnroll records per iteration (a short last iteration is
-// filled with the empty record at index kFwdBatch), summed in 32-record blocks
-// that are added to the totals (two-level summation).
+// thread's strip, kFwdUnroll records per iteration (the list is padded to a
+// multiple of kFwdUnroll with the empty record at index kFwdBatch), summed in
+// 32-record blocks that are added to the totals (two-level summation).
 template <int kMode, bool kCount, int kStrip, bool kTest, bool kClamp>
 __device__ __forceinline__ void fwd_list(const float4 *s0, const float4 *s1, const float4 *s2, const float *ssign,
                                          const uint16_t *list, int cnt, int ky, int sx, bool in_view_row, int x0,
@@ -100,7 +100,7 @@ __device__ __forceinline__ void fwd_list(const float4 *s0, const float4 *s1, con
         for (int i = jb; i < je; i += kFwdUnroll) {
 #pragma unroll
             for (int u = 0; u < kFwdUnroll; ++u) {
-                const int j = i + u < je ? list[i + u] : kFwdBatch;
+                const int j = list[i + u];
                 fwd_splat<kMode, kCount, kStrip, kTest, kClamp>(s0, s1, s2, ssign, j, ky, sx, in_view_row, x0, W,
                                                                 b01, b2q, bl, T, n_contrib);
             }
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
     __shared__ float ssign[kMode == kRasterSums ? kFwdBatch + 1 : 1];
     // per batch: the records whose cutoff ellipse contains the whole tile (every warp takes them
     // without cutoff tests), and per warp the other records whose ellipse reaches its rows
-    __shared__ uint16_t flist[kFwdBatch], wlist[kWarps][kFwdBatch];
+    __shared__ uint16_t flist[kFwdBatch + kFwdUnroll], wlist[kWarps][kFwdBatch + kFwdUnroll];
     __shared__ int fcnt, wcnt[kWarps];
     __shared__ float red[kFwdThreads / 32];
     // the tile's sums (P_r, P_g, P_b, Q, T or log T) by pixel, for the epilogue's row-contiguous mapping
@@ -268,7 +268,15 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
                 }
             }
             const bool clamp = __syncthreads_or(may_clamp) != 0;
-            const int nf = fcnt, nw = wcnt[warp];
+            const int nf0 = fcnt, nw0 = wcnt[warp];
+            // pad both lists of this warp to a multiple of kFwdUnroll with the empty record (every
+            // warp pads the shared list with the same values past its end)
+            if ((tid & 31) < kFwdUnroll - 1) {
+                flist[nf0 + (tid & 31)] = (uint16_t)kFwdBatch;
+                wlist[warp][nw0 + (tid & 31)] = (uint16_t)kFwdBatch;
+            }
+            __syncwarp();
+            const int nf = (nf0 + kFwdUnroll - 1) & ~(kFwdUnroll - 1), nw = (nw0 + kFwdUnroll - 1) & ~(kFwdUnroll - 1);
             if (clamp) {
                 fwd_list<kMode, kCount, kStrip, false, true>(s0, s1, s2, ssign, flist, nf, ky, sx, in_view_row, x0, vd.W,
                                                              P01, P2Q, T, n_contrib);
