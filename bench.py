@@ -1031,7 +1031,7 @@ def main():
         total_E = float(head["E"])
     value = total_E / (ms * 1e-3)
 
-    set_active_ms = commit_inc_ms = None
+    set_active_ms = commit_inc_ms = async_host_ms = async_dev_ms = sync_host_ms = None
     e2e_ms, h2d, d2h = None, 0, 0
     train = dssim = None
     if not args.no_e2e:
@@ -1041,8 +1041,12 @@ def main():
             r.set_active(make(HEADLINE_FRACTION), stream=stream)
             r.commit_frozen(sp, cam, 0, mode="recompute", stream=stream)
             m2 = make(HEADLINE_FRACTION, seed_shift=1)
+            m3 = make(HEADLINE_FRACTION, seed_shift=2)
             stream.synchronize()
             a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            # a GPU sleep ahead of the events keeps the stream busy while the host enqueues the
+            # call, so that the events time the device work alone (the host time is taken apart)
+            torch.cuda._sleep(2_000_000)
             a.record(stream)
             r.set_active(m2, stream=stream)
             b.record(stream)
@@ -1050,6 +1054,22 @@ def main():
             c.record(stream)
             stream.synchronize()
             set_active_ms, commit_inc_ms = a.elapsed_time(b), b.elapsed_time(c)
+            # the same update without the host wait (sparseoit_set_active_async); then the
+            # headline's changed set again
+            torch.cuda._sleep(2_000_000)
+            a.record(stream)
+            t0 = time.perf_counter()
+            r.set_active(m3, stream=stream, asynchronous=True)
+            async_host_ms = (time.perf_counter() - t0) * 1e3
+            b.record(stream)
+            stream.synchronize()
+            async_dev_ms = a.elapsed_time(b)
+            # host time of the synchronising call on an idle stream (back to the changed set)
+            t0 = time.perf_counter()
+            r.set_active(m2, stream=stream)
+            sync_host_ms = (time.perf_counter() - t0) * 1e3
+            r.commit_frozen(sp, cam, 0, mode="recompute", stream=stream)
+            stream.synchronize()
 
         # end to end through the public API with host buffers, on the stage layout of the headline
         # step: every step copies the active rows (the parameters the step trains) and the target from
@@ -1345,7 +1365,11 @@ def main():
                       for f, v in results.items()},
         "per_kernel_ms_full": None if full is None or not full["prof"] else {
             k: {"launches": n_, "avg_ms": t_ / max(1, n_)} for k, (n_, t_) in full["prof"].items()},
-        "stage_update": {"set_active_ms": set_active_ms, "commit_incremental_ms": commit_inc_ms},
+        "stage_update": {"set_active_ms": set_active_ms, "set_active_host_call_ms": sync_host_ms,
+                         "commit_incremental_ms": commit_inc_ms,
+                         "set_active_async": {"host_call_ms": async_host_ms, "device_ms": async_dev_ms},
+                         "timing": "device times from CUDA events with the call queued behind a GPU sleep; "
+                                   "host call times with perf_counter"},
         "per_kernel_ms": per_kernel,
         "roofline": roofline,
         "fp32": {"peak_tflops": peak_tf, "per_kernel": fp32},

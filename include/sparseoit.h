@@ -186,6 +186,17 @@ int sparseoit_destroy(sparseoit_ctx *ctx);
  * host needs |A| to size later launches). */
 int sparseoit_set_active(sparseoit_ctx *ctx, const uint8_t *d_mask, int64_t n, void *stream);
 
+/* Sec. 4.1, the same update of A without waiting: the compaction and the
+ * copy of the four set sizes to host memory are enqueued on `stream` and the
+ * call returns.  The first later call on this context that needs the sizes
+ * (every call that takes splats, sparseoit_get_active, sparseoit_adam_step,
+ * sparseoit_gather_active / sparseoit_scatter_active, the next
+ * set_active) waits for that copy alone, so the host can prepare the next
+ * step meanwhile.  d_mask must stay valid and unchanged until `stream` has
+ * run the compaction.  Same arguments and errors as sparseoit_set_active;
+ * an error of the compaction itself surfaces at that later wait. */
+int sparseoit_set_active_async(sparseoit_ctx *ctx, const uint8_t *d_mask, int64_t n, void *stream);
+
 /* The active index list (device, ascending, int32) and |A|.  The pointer
  * stays valid until the next set_active. */
 int sparseoit_get_active(sparseoit_ctx *ctx, const int32_t **d_idx, int64_t *n_active);

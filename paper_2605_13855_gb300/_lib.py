@@ -32,7 +32,8 @@ ERROR_NAMES = {ERR_INVALID_ARG: "INVALID_ARG", ERR_OOM: "OOM", ERR_CUDA: "CUDA",
 
 # Every entry point declared in include/sparseoit.h.
 EXPORTED = (
-    "sparseoit_create", "sparseoit_destroy", "sparseoit_set_active", "sparseoit_get_active",
+    "sparseoit_create", "sparseoit_destroy", "sparseoit_set_active", "sparseoit_set_active_async",
+    "sparseoit_get_active",
     "sparseoit_commit_frozen", "sparseoit_get_frozen", "sparseoit_set_frozen", "sparseoit_forward",
     "sparseoit_backward",
     "sparseoit_reserve_pairs", "sparseoit_status", "sparseoit_last_counts", "sparseoit_set_counting",
@@ -112,6 +113,7 @@ def load(path: str = LIB_PATH):
             "sparseoit_create": ([P(vp), i64, i32, P(i32), P(i32), P(Config)], ctypes.c_int),
             "sparseoit_destroy": ([vp], ctypes.c_int),
             "sparseoit_set_active": ([vp, vp, i64, vp], ctypes.c_int),
+            "sparseoit_set_active_async": ([vp, vp, i64, vp], ctypes.c_int),
             "sparseoit_get_active": ([vp, P(vp), P(i64)], ctypes.c_int),
             "sparseoit_commit_frozen": ([vp, P(Splats), P(Camera), i32, i32, vp], ctypes.c_int),
             "sparseoit_get_frozen": ([vp, i32, P(vp)], ctypes.c_int),

@@ -52,6 +52,10 @@ struct sparseoit_ctx {
     int64_t *d_totals = nullptr;
     int64_t *h_totals = nullptr;  // pinned
     int64_t n_active = 0, n_comp = 0, n_plus = 0, n_minus = 0;
+    // set by sparseoit_set_active_async: the counts above are still being copied into h_totals;
+    // ev_counts completes with the copy
+    bool counts_pending = false;
+    cudaEvent_t ev_counts = nullptr;
     int64_t generation = 0;       // number of set_active calls
     bool have_mask = false;
     std::vector<int64_t> view_gen;
@@ -162,8 +166,25 @@ static cudaError_t grow(T **p, int64_t *cap, int64_t want) {
     return e;
 }
 
+// The host copies of |A|, |complement|, |D+|, |D-|: after sparseoit_set_active_async they are
+// still in flight, and the first call that needs them waits here for the copy.
+static int sync_counts(sparseoit_ctx *ctx) {
+    if (!ctx->counts_pending) return SPARSEOIT_OK;
+    ctx->counts_pending = false;
+    CK(cudaEventSynchronize(ctx->ev_counts), "wait for the active-set counts");
+    ctx->n_active = ctx->h_totals[0];
+    ctx->n_comp = ctx->h_totals[1];
+    ctx->n_plus = ctx->h_totals[2];
+    ctx->n_minus = ctx->h_totals[3];
+    return SPARSEOIT_OK;
+}
+
 static int check_splats(sparseoit_ctx *ctx, const sparseoit_splats *s, bool allow_active_rows) {
     if (!s) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "splats is null");
+    {
+        const int rc = sync_counts(ctx);
+        if (rc) return rc;
+    }
     if (s->rows == SPARSEOIT_ROWS_ACTIVE) {
         if (!allow_active_rows)
             return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "this call needs the splats in rows by splat");
@@ -408,6 +429,7 @@ int sparseoit_create(sparseoit_ctx **out, int64_t max_splats, int32_t n_views, c
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_blk, (size_t)compact_scratch_ints(n) * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_totals, 4 * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->h_totals, 4 * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_counts, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_pairs, (size_t)ctx->pair_cap * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_queue, 2 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_status, sizeof(unsigned));
@@ -433,6 +455,10 @@ int sparseoit_destroy(sparseoit_ctx *ctx) {
                     ctx->d_contrib, ctx->d_upd_image, ctx->d_upd_loss, ctx->d_ssim_abc, ctx->d_ssim_sums,
                     ctx->d_idx_all};
     for (void *p : bufs) if (p) cudaFree(p);
+    if (ctx->ev_counts) {
+        cudaEventSynchronize(ctx->ev_counts);  // no copy into h_totals may be left in flight
+        cudaEventDestroy(ctx->ev_counts);
+    }
     if (ctx->h_totals) cudaFreeHost(ctx->h_totals);
     for (auto &m : ctx->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
@@ -440,9 +466,13 @@ int sparseoit_destroy(sparseoit_ctx *ctx) {
     return SPARSEOIT_OK;
 }
 
-int sparseoit_set_active(sparseoit_ctx *ctx, const uint8_t *d_mask, int64_t n, void *stream) {
-    NvtxRange nvtx__("sparseoit_set_active");
+// set_active and set_active_async: `wait` selects whether the host waits for the counts now.
+static int set_active_impl(sparseoit_ctx *ctx, const uint8_t *d_mask, int64_t n, void *stream, bool wait) {
     if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
+    {
+        const int rc = sync_counts(ctx);  // h_totals is about to be overwritten
+        if (rc) return rc;
+    }
     if (!d_mask && n > 0) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "mask is null");
     if (n != ctx->N) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "mask length differs from max_splats");
     cudaStream_t st = (cudaStream_t)stream;
@@ -456,11 +486,16 @@ int sparseoit_set_active(sparseoit_ctx *ctx, const uint8_t *d_mask, int64_t n, v
     CK_LAUNCH("compaction kernels");
     CK(cudaMemcpyAsync(ctx->h_totals, ctx->d_totals, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, st),
        "copy active counts");
-    CK(cudaStreamSynchronize(st), "set_active sync");
-    ctx->n_active = ctx->h_totals[0];
-    ctx->n_comp = ctx->h_totals[1];
-    ctx->n_plus = ctx->h_totals[2];
-    ctx->n_minus = ctx->h_totals[3];
+    if (wait) {
+        CK(cudaStreamSynchronize(st), "set_active sync");
+        ctx->n_active = ctx->h_totals[0];
+        ctx->n_comp = ctx->h_totals[1];
+        ctx->n_plus = ctx->h_totals[2];
+        ctx->n_minus = ctx->h_totals[3];
+    } else {
+        CK(cudaEventRecord(ctx->ev_counts, st), "record the active-count copy");
+        ctx->counts_pending = true;
+    }
     ctx->cur ^= 1;
     ctx->have_mask = true;
     ctx->generation += 1;
@@ -468,9 +503,23 @@ int sparseoit_set_active(sparseoit_ctx *ctx, const uint8_t *d_mask, int64_t n, v
     return SPARSEOIT_OK;
 }
 
+int sparseoit_set_active(sparseoit_ctx *ctx, const uint8_t *d_mask, int64_t n, void *stream) {
+    NvtxRange nvtx__("sparseoit_set_active");
+    return set_active_impl(ctx, d_mask, n, stream, true);
+}
+
+int sparseoit_set_active_async(sparseoit_ctx *ctx, const uint8_t *d_mask, int64_t n, void *stream) {
+    NvtxRange nvtx__("sparseoit_set_active_async");
+    return set_active_impl(ctx, d_mask, n, stream, false);
+}
+
 int sparseoit_get_active(sparseoit_ctx *ctx, const int32_t **d_idx, int64_t *n_active) {
     if (!ctx || !d_idx || !n_active) return SPARSEOIT_ERR_INVALID_ARG;
     if (!ctx->have_mask) return fail(ctx, SPARSEOIT_ERR_STATE, "no active set yet");
+    {
+        const int rc = sync_counts(ctx);
+        if (rc) return rc;
+    }
     *d_idx = ctx->d_idx_active;
     *n_active = ctx->n_active;
     return SPARSEOIT_OK;
@@ -728,6 +777,10 @@ int sparseoit_adam_step(sparseoit_ctx *ctx, const sparseoit_grads *grads, sparse
     if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
     if (!grads || !params || !m || !v || !cfg) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "adam: null argument");
     if (!ctx->have_mask) return fail(ctx, SPARSEOIT_ERR_STATE, "adam before set_active");
+    {
+        const int rc = sync_counts(ctx);
+        if (rc) return rc;
+    }
     if (cfg->step < 1 || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) || !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) ||
         !(cfg->eps > 0.f))
         return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "adam: need step >= 1, 0 <= beta < 1, eps > 0");
@@ -832,6 +885,10 @@ static int rows_copy(sparseoit_ctx *ctx, const sparseoit_rows *src, sparseoit_ro
     if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
     if (!src || !dst) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "rows: null argument");
     if (!ctx->have_mask) return fail(ctx, SPARSEOIT_ERR_STATE, "rows: before set_active");
+    {
+        const int rc = sync_counts(ctx);
+        if (rc) return rc;
+    }
     if (sh_dtype != SPARSEOIT_F32 && sh_dtype != SPARSEOIT_BF16)
         return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "rows: unknown sh_dtype");
     const float *s6[6] = {src->means, src->quats, src->log_scales, src->opacity_logits, src->sh_color, src->sh_weight};

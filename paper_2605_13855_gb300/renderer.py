@@ -136,7 +136,8 @@ class Renderer:
         rc = self.lib.sparseoit_create(ctypes.byref(self._ctx), self.n, nv, ws, hs, ctypes.byref(cfg))
         if rc != _lib.OK:
             raise SparseOITError(rc, self.lib.sparseoit_last_error(None).decode())
-        self.n_active = 0
+        self._n_active = 0
+        self._pending_mask = None  # the mask of an asynchronous set_active, kept alive until its count is read
         self.forward_id = 0
         self._last_views: List[int] = []
         self._keep = None
@@ -158,18 +159,36 @@ class Renderer:
             pass
 
     # -------------------------------------------------------- active set
-    def set_active(self, mask: torch.Tensor, stream=None):
-        """Sec. 4.1: set A from a [N] bool / uint8 CUDA mask (synchronises)."""
+    def set_active(self, mask: torch.Tensor, stream=None, asynchronous: bool = False):
+        """Sec. 4.1: set A from a [N] bool / uint8 CUDA mask.  By default the call synchronises the
+        stream; asynchronous=True enqueues the compaction and returns, and |A| is read (waiting for
+        that compaction only) when n_active or a later call first needs it."""
         if mask.dtype == torch.bool:
             mask = mask.to(torch.uint8)
         if mask.dtype != torch.uint8 or not mask.is_cuda or mask.numel() != self.n:
             raise ValueError("mask must be a CUDA uint8/bool tensor of n_splats entries")
         mask = mask.contiguous()
-        self._check(self.lib.sparseoit_set_active(self._ctx, ctypes.c_void_p(mask.data_ptr()), self.n,
-                                                  ctypes.c_void_p(_stream_ptr(stream))))
+        fn = self.lib.sparseoit_set_active_async if asynchronous else self.lib.sparseoit_set_active
+        self._check(fn(self._ctx, ctypes.c_void_p(mask.data_ptr()), self.n, ctypes.c_void_p(_stream_ptr(stream))))
+        if asynchronous:
+            self._pending_mask = mask
+            self._n_active = None
+        else:
+            self._pending_mask = None
+            self._read_n_active()
+
+    def _read_n_active(self):
         p, na = ctypes.c_void_p(), ctypes.c_int64()
         self._check(self.lib.sparseoit_get_active(self._ctx, ctypes.byref(p), ctypes.byref(na)))
-        self.n_active = int(na.value)
+        self._n_active = int(na.value)
+        self._pending_mask = None
+
+    @property
+    def n_active(self) -> int:
+        """|A| of the current active set (after an asynchronous set_active: waits for its count)."""
+        if self._n_active is None:
+            self._read_n_active()
+        return self._n_active
 
     def active_indices(self) -> torch.Tensor:
         """Ascending int32 indices of A (a copy)."""
@@ -355,7 +374,8 @@ class Renderer:
         # the call ends with set_active on the new mask
         idx, na = ctypes.c_void_p(), ctypes.c_int64()
         self._check(self.lib.sparseoit_get_active(self._ctx, ctypes.byref(idx), ctypes.byref(na)))
-        self.n_active = int(na.value)
+        self._n_active = int(na.value)
+        self._pending_mask = None
         self.forward_id += 1
         return mask, [int(sel[k]) for k in range(int(n_sub))], scratch
 
