@@ -68,6 +68,17 @@ struct Batch {
     ViewDesc v[kMaxViews];
 };
 
+// Programmatic dependent launch (sm_90 and later).  The kernels of a step
+// are launched so that a kernel's blocks may become resident while the
+// kernel before it on the stream drains.  A kernel calls pdl_wait() before
+// it reads anything that kernel writes (griddepcontrol.wait returns once the
+// previous grid has completed and its memory operations are visible), and
+// pdl_allow_next() after that wait, so that the next kernel's early part
+// only ever runs once every kernel before this one has completed.  Launched
+// without the attribute, both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_allow_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // The tile scan of this batch's binning gave up (a bounded wait ran out): its
 // offsets and tile order are incomplete, so the kernels after it do nothing.
 // (Read through the read-only cache: no kernel after the scan writes the

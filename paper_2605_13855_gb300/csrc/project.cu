@@ -77,8 +77,10 @@ template <typename ShT, int G>
 __global__ void __launch_bounds__(256, 3) project_kernel(const __grid_constant__ Batch b, SplatPtrs sp,
                                                       const int *__restrict__ list1, int n1,
                                                       const int *__restrict__ list2, int n2, float4 *__restrict__ rec,
-                                                      float4 *__restrict__ ext, int *__restrict__ tile_count) {
+                                                      float4 *__restrict__ ext, int *__restrict__ tile_count,
+                                                      float4 *__restrict__ sgrad_zero) {
     constexpr int J = 16 / G;
+    pdl_allow_next();  // launched after everything before it completed: the scan may become resident
     const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G);  // uniform in a group
     const int k = threadIdx.x & (G - 1);
     const int n_list = n1 + n2;
@@ -155,25 +157,31 @@ __global__ void __launch_bounds__(256, 3) project_kernel(const __grid_constant__
                 }
             }
         }
-        // the four 16-byte outputs, lane k of the group storing outputs k, k + G, ...
+        // the four 16-byte outputs, lane k of the group storing outputs k, k + G, ...; and the
+        // record's three rows of screen-space gradient sums zeroed for the backward raster's atomics
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (G >= 4) {
             if (k == 0) rec[3 * qidx + 0] = r0;
             else if (k == 1) rec[3 * qidx + 1] = r1;
             else if (k == 2) rec[3 * qidx + 2] = r2;
             else if (k == 3) ext[qidx] = e;
+            if (sgrad_zero && k < 3) sgrad_zero[3 * qidx + k] = z4;
         } else if (G == 2) {
             if (k == 0) {
                 rec[3 * qidx + 0] = r0;
                 rec[3 * qidx + 2] = r2;
+                if (sgrad_zero) sgrad_zero[3 * qidx + 0] = sgrad_zero[3 * qidx + 2] = z4;
             } else {
                 rec[3 * qidx + 1] = r1;
                 ext[qidx] = e;
+                if (sgrad_zero) sgrad_zero[3 * qidx + 1] = z4;
             }
         } else {
             rec[3 * qidx + 0] = r0;
             rec[3 * qidx + 1] = r1;
             rec[3 * qidx + 2] = r2;
             ext[qidx] = e;
+            if (sgrad_zero) sgrad_zero[3 * qidx + 0] = sgrad_zero[3 * qidx + 1] = sgrad_zero[3 * qidx + 2] = z4;
         }
     }
 }
@@ -221,6 +229,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const int *__r
     __shared__ int bad_s;
     __shared__ int cls[kLoadClasses];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    pdl_wait();  // the projection's tile counts
+    pdl_allow_next();
     if (tid == 0) part_s = atomicAdd(sc.ticket, 1);
     for (int k = tid; k < kLoadClasses; k += kScanThreads) cls[k] = 0;
     __syncthreads();
@@ -359,18 +369,30 @@ __global__ void __launch_bounds__(256, 8) scatter_kernel(const __grid_constant__
                                                          uint32_t *__restrict__ pairs, int64_t cap,
                                                          const int *__restrict__ count, ScanScratch sc, int *order,
                                                          int order_blocks) {
-    if ((int)blockIdx.x < order_blocks && !bin_failed(b)) place_tile_order(count, b.total_tiles, sc, order, blockIdx.x);
     const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
+    // the first view's record, written by the projection (complete before the scan got past its own
+    // wait), is read while the scan may still be running
+    float4 e = make_float4(-1.f, 0.f, 0.f, 0.f), r0 = e;
+    float B2 = 0.f;
+    if (r < b.n_list) {
+        e = ext[r];
+        r0 = rec[3 * (int64_t)r + 0];
+        B2 = rec[3 * (int64_t)r + 1].x;
+    }
+    pdl_wait();  // the scan's offsets, cursors, class histogram and status
+    pdl_allow_next();
+    if ((int)blockIdx.x < order_blocks && !bin_failed(b)) place_tile_order(count, b.total_tiles, sc, order, blockIdx.x);
     if (r >= b.n_list) return;  // whole warps leave together
     for (int v = 0; v < b.n_views; ++v) {
         const ViewDesc &vd = b.v[v];
         const int64_t qidx = (int64_t)v * b.n_list + r;
-        // the loads are issued together (the record is read even when the splat is culled), the
-        // status word with them: if the tile scan gave up, its offsets are incomplete
-        const float4 e = ext[qidx];
-        const float4 r0 = rec[3 * qidx + 0];
-        const float B2 = rec[3 * qidx + 1].x;
+        if (v > 0) {  // the loads are issued together (the record is read even when the splat is culled)
+            e = ext[qidx];
+            r0 = rec[3 * qidx + 0];
+            B2 = rec[3 * qidx + 1].x;
+        }
+        // if the tile scan gave up, its offsets are incomplete
         const unsigned stat = __ldg(b.status);
         int ty0, ty1;
         if (stat & kStatusTimeout) return;
@@ -416,42 +438,46 @@ __global__ void __launch_bounds__(256, 8) scatter_kernel(const __grid_constant__
 
 template <int G>
 static void launch_project_g(const Batch &b, const SplatPtrs &sp, bool bf16, const int *list1, int n1,
-                             const int *list2, int n2, float4 *rec, float4 *ext, int *tile_count, cudaStream_t st) {
+                             const int *list2, int n2, float4 *rec, float4 *ext, int *tile_count, float4 *sgrad_zero,
+                             cudaStream_t st) {
     const int grid = (int)(((int64_t)(n1 + n2) * G + 255) / 256);
     if (bf16)
-        project_kernel<__nv_bfloat16, G><<<grid, 256, 0, st>>>(b, sp, list1, n1, list2, n2, rec, ext, tile_count);
+        project_kernel<__nv_bfloat16, G>
+            <<<grid, 256, 0, st>>>(b, sp, list1, n1, list2, n2, rec, ext, tile_count, sgrad_zero);
     else
-        project_kernel<float, G><<<grid, 256, 0, st>>>(b, sp, list1, n1, list2, n2, rec, ext, tile_count);
+        project_kernel<float, G><<<grid, 256, 0, st>>>(b, sp, list1, n1, list2, n2, rec, ext, tile_count, sgrad_zero);
 }
 
 int launch_project(const Batch &b, const SplatPtrs &sp, bool bf16, int lanes, const int *list1, int n1,
-                   const int *list2, int n2, float4 *rec, float4 *ext, int *tile_count, cudaStream_t st) {
+                   const int *list2, int n2, float4 *rec, float4 *ext, int *tile_count, float4 *sgrad_zero,
+                   cudaStream_t st) {
     if (n1 + n2 == 0) return 0;
     if (lanes == 16)
-        launch_project_g<16>(b, sp, bf16, list1, n1, list2, n2, rec, ext, tile_count, st);
+        launch_project_g<16>(b, sp, bf16, list1, n1, list2, n2, rec, ext, tile_count, sgrad_zero, st);
     else if (lanes == 2)
-        launch_project_g<2>(b, sp, bf16, list1, n1, list2, n2, rec, ext, tile_count, st);
+        launch_project_g<2>(b, sp, bf16, list1, n1, list2, n2, rec, ext, tile_count, sgrad_zero, st);
     else if (lanes == 1)
-        launch_project_g<1>(b, sp, bf16, list1, n1, list2, n2, rec, ext, tile_count, st);
+        launch_project_g<1>(b, sp, bf16, list1, n1, list2, n2, rec, ext, tile_count, sgrad_zero, st);
     else
-        launch_project_g<4>(b, sp, bf16, list1, n1, list2, n2, rec, ext, tile_count, st);
+        launch_project_g<4>(b, sp, bf16, list1, n1, list2, n2, rec, ext, tile_count, sgrad_zero, st);
     return 0;
 }
 
 int launch_scan_tiles(const int *count, int total, int *offsets, int *cursor, ScanScratch sc, int64_t cap,
-                      unsigned *status, int64_t *pairs_out, int withhold, cudaStream_t st) {
-    scan_tiles_kernel<<<scan_partitions(total), kScanThreads, 0, st>>>(count, total, offsets, cursor, sc, cap, status,
-                                                                       pairs_out, withhold);
+                      unsigned *status, int64_t *pairs_out, int withhold, bool pdl, cudaStream_t st) {
+    launch_kernel(scan_tiles_kernel, dim3(scan_partitions(total)), dim3(kScanThreads), st, pdl, count, total, offsets,
+                  cursor, sc, cap, status, pairs_out, withhold);
     return 0;
 }
 
 int launch_scatter(const Batch &b, const float4 *rec, const float4 *ext, int *cursor, uint32_t *pairs, int64_t cap,
-                   const int *count, ScanScratch sc, int *order, cudaStream_t st) {
+                   const int *count, ScanScratch sc, int *order, bool pdl, cudaStream_t st) {
     const int order_blocks = order ? (b.total_tiles + kScanThreads - 1) / kScanThreads : 0;
     const int scatter_blocks = (int)(((int64_t)b.n_list * 32 + 255) / 256);
     const int grid = scatter_blocks > order_blocks ? scatter_blocks : order_blocks;
     if (grid == 0) return 0;
-    scatter_kernel<<<grid, 256, 0, st>>>(b, rec, ext, cursor, pairs, cap, count, sc, order, order_blocks);
+    launch_kernel(scatter_kernel, dim3(grid), dim3(256), st, pdl, b, rec, ext, cursor, pairs, cap, count, sc, order,
+                  order_blocks);
     return 0;
 }
 

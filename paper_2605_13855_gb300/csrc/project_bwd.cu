@@ -61,8 +61,10 @@ __device__ __forceinline__ void staged_sh_run(const float4 *hc, const float4 *hw
 template <typename ShT>
 __global__ void __launch_bounds__(kChainThreads, 3) project_bwd_kernel(const __grid_constant__ Batch b, SplatPtrs sp,
                                                           const int *__restrict__ list, int n,
-                                                          const float4 *__restrict__ sgrad, GradPtrs out) {
+                                                          const float4 *__restrict__ sgrad, GradPtrs out,
+                                                          float *__restrict__ sig_part, unsigned *sig_count) {
     __shared__ float red[4];
+    __shared__ int last_s;
     __shared__ float4 shc[kChainThreads * kRowC4], shw[kChainThreads * kRowW4];
     const int r0 = blockIdx.x * kChainThreads, nb = min(kChainThreads, n - r0);
     stage_sh_rows<ShT>(sp, list, r0, nb, shc, shw);
@@ -80,6 +82,10 @@ __global__ void __launch_bounds__(kChainThreads, 3) project_bwd_kernel(const __g
         for (int k = 0; k < 3; ++k) ls[k] = __ldg(sp.log_scales + 3 * (int64_t)pi + k);
         const float ol = __ldg(sp.opacity_logits + pi);
         const float o = 1.f / (1.f + expf(-ol));
+        // the staged rows and the parameters above are inputs of the step; the screen-space sums
+        // below are the backward raster's output
+        pdl_wait();
+        pdl_allow_next();
 
         float g_mu[3] = {0.f, 0.f, 0.f}, g_q[4] = {0.f, 0.f, 0.f, 0.f}, g_ls[3] = {0.f, 0.f, 0.f}, g_ol = 0.f;
         float g_h[48], g_hw[16];
@@ -255,25 +261,46 @@ __global__ void __launch_bounds__(kChainThreads, 3) project_bwd_kernel(const __g
         }
         *dst = v;
     }
-    // dL/dsigma: block reduction, one atomic per block
+    // dL/dsigma: the block's sum to sig_part, then the last block to finish sums the partials in
+    // block order (the same result on every run) and resets the counter for the next launch
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) gsig_local += __shfl_xor_sync(0xffffffffu, gsig_local, off);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = gsig_local;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const float s = red[0] + red[1] + red[2] + red[3];
-        if (s != 0.f) atomicAdd(out.sigma, s);
+        sig_part[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
+        __threadfence();
+        last_s = atomicAdd(sig_count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last_s) return;
+    __threadfence();
+    float sum = 0.f;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += kChainThreads) sum += __ldcg(sig_part + k);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    __syncthreads();  // red[] is read above by thread 0 only; reuse it
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const float total = red[0] + red[1] + red[2] + red[3];
+        *out.sigma = out.accumulate ? *out.sigma + total : total;
+        *sig_count = 0u;
     }
 }
 
+int project_bwd_blocks(int n) { return (n + kChainThreads - 1) / kChainThreads; }
+
 int launch_project_bwd(const Batch &b, const SplatPtrs &sp, bool bf16, const int *list, int n, const float4 *sgrad,
-                       GradPtrs out, cudaStream_t st) {
+                       GradPtrs out, float *sig_part, unsigned *sig_count, bool pdl, cudaStream_t st) {
     if (n == 0) return 0;
-    const int grid = (n + kChainThreads - 1) / kChainThreads;
+    const int grid = project_bwd_blocks(n);
     if (bf16)
-        project_bwd_kernel<__nv_bfloat16><<<grid, kChainThreads, 0, st>>>(b, sp, list, n, sgrad, out);
+        launch_kernel(project_bwd_kernel<__nv_bfloat16>, dim3(grid), dim3(kChainThreads), st, pdl, b, sp, list, n,
+                      sgrad, out, sig_part, sig_count);
     else
-        project_bwd_kernel<float><<<grid, kChainThreads, 0, st>>>(b, sp, list, n, sgrad, out);
+        launch_kernel(project_bwd_kernel<float>, dim3(grid), dim3(kChainThreads), st, pdl, b, sp, list, n, sgrad,
+                      out, sig_part, sig_count);
     return 0;
 }
 

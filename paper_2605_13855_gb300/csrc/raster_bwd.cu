@@ -289,13 +289,24 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks)
         const int lt = gt - vd.tile_base;
         const int ty = lt / vd.tiles_x, tx = lt - ty * vd.tiles_x;
         const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-        load_tile_state<kBwdThreads>(vd, tx, ty, S);
+        // the pixel state is the forward raster's output: it is loaded after pdl_wait, once the
+        // tile's pairs are sorted (pairs, records and tile order are older, the scatter's and the
+        // projection's), so that the sort overlaps the end of the forward
+        bool have_state = false;
+        auto state_in = [&]() {
+            if (have_state) return;
+            pdl_wait();
+            pdl_allow_next();
+            load_tile_state<kBwdThreads>(vd, tx, ty, S);
+            have_state = true;
+        };
 
         const int start = offsets[gt];
         const int end = (int)min((int64_t)offsets[gt + 1], cap);
         const float ox = (float)(tx * kTile) + 0.5f, oy = (float)(ty * kTile) + 0.5f;
 
         if constexpr (!kSort) {
+            if (start < end) state_in();
             __syncthreads();
             for (int cb0 = start + warp * 32; cb0 < end; cb0 += kBwdThreads) {
                 const int idx = cb0 + lane;
@@ -307,7 +318,7 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks)
                 if (c0 > start) __syncthreads();  // the previous chunk's arrays are consumed
                 if (tid < 32) hist[tid] = 0;
                 if (tid == 0) next_group = 0;
-                __syncthreads();  // also: the state is loaded
+                __syncthreads();
                 for (int i = tid; i < nc; i += kBwdThreads) {
                     const uint32_t q = pairs[c0 + i];
                     const int key = q < nrec ? pair_key(rec, q, ox, oy) : kBwdKeys - 1;
@@ -327,7 +338,8 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks)
                 }
                 __syncthreads();
                 for (int i = tid; i < nc; i += kBwdThreads) sorted[hist[keys[i]] + slot[i]] = pairs[c0 + i];
-                __syncthreads();
+                state_in();
+                __syncthreads();  // the sorted pairs and the state
                 for (;;) {
                     int g = 0;
                     if (lane == 0) g = atomicAdd(&next_group, 1);
@@ -370,7 +382,7 @@ int launch_prep_state(const Batch &b, const float bg[3], cudaStream_t st) {
 
 template <bool kSort>
 static void launch_bwd(const Batch &b, const float4 *rec, const int *offsets, const uint32_t *pairs, int64_t cap,
-                       uint32_t nrec, float4 *sgrad, int *queue, cudaStream_t st) {
+                       uint32_t nrec, float4 *sgrad, int *queue, bool pdl, cudaStream_t st) {
     auto kern = raster_bwd_kernel<kSort>;
     int grid = b.total_tiles;
     if (queue) {  // persistent: as many blocks as fit on the device at once, at most one per tile
@@ -381,18 +393,19 @@ static void launch_bwd(const Batch &b, const float4 *rec, const int *offsets, co
         const int g = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
         grid = g < grid ? g : grid;
         cudaMemsetAsync(queue, 0, sizeof(int), st);
+        pdl = false;  // the operation just before the raster is this memset
     }
-    kern<<<grid, kBwdThreads, 0, st>>>(b, rec, offsets, pairs, cap, nrec, sgrad, queue);
+    launch_kernel(kern, dim3(grid), dim3(kBwdThreads), st, pdl, b, rec, offsets, pairs, cap, nrec, sgrad, queue);
 }
 
 int launch_raster_bwd(const Batch &b, int walk, const float4 *rec, const int *offsets, const uint32_t *pairs,
-                      int64_t cap, float4 *sgrad, int *queue, cudaStream_t st) {
+                      int64_t cap, float4 *sgrad, int *queue, bool pdl, cudaStream_t st) {
     if (b.total_tiles == 0) return 0;
     const uint32_t nrec = (uint32_t)((int64_t)b.n_views * b.n_list);
     if (walk == kBwdWalkArena)
-        launch_bwd<false>(b, rec, offsets, pairs, cap, nrec, sgrad, queue, st);
+        launch_bwd<false>(b, rec, offsets, pairs, cap, nrec, sgrad, queue, pdl, st);
     else
-        launch_bwd<true>(b, rec, offsets, pairs, cap, nrec, sgrad, queue, st);
+        launch_bwd<true>(b, rec, offsets, pairs, cap, nrec, sgrad, queue, pdl, st);
     return 0;
 }
 

@@ -152,6 +152,8 @@ __global__ void __launch_bounds__(kTilePix / kStrip, kStrip == 1 ? 4 : (kStrip =
     __shared__ unsigned red_n[kFwdThreads / 32];
 
     __shared__ int item_s;
+    pdl_wait();  // the scatter's pairs and tile order
+    pdl_allow_next();
     if (bin_failed(b)) return;  // the binning scan gave up: offsets and tile order are incomplete
     // queue == null: this block's tile (block_tile); else a persistent block that takes tiles from the
     // queue (in the raster order) until none is left
@@ -399,52 +401,58 @@ static int persistent_grid(K kernel, int threads, int total_tiles) {
 template <int kMode, bool kCount, int kStrip>
 static void launch_one(const Batch &b, const float4 *rec, const int *offsets, const uint32_t *pairs, int64_t cap,
                        uint32_t nrec, const float bg[3], float *loss, unsigned long long *contrib, int *queue,
-                       cudaStream_t st) {
+                       bool pdl, cudaStream_t st) {
     constexpr int kThreads = kTilePix / kStrip;
     auto kern = raster_fwd_kernel<kMode, kCount, kStrip>;
     const int grid = queue ? persistent_grid(kern, kThreads, b.total_tiles) : b.total_tiles;
-    kern<<<grid, kThreads, 0, st>>>(b, rec, offsets, pairs, cap, nrec, bg[0], bg[1], bg[2], loss, contrib, queue);
+    launch_kernel(kern, dim3(grid), dim3(kThreads), st, pdl, b, rec, offsets, pairs, cap, nrec, bg[0], bg[1], bg[2],
+                  loss, contrib, queue);
 }
 
 template <int kMode, int kStrip>
 static void launch_strip(const Batch &b, bool count, const float4 *rec, const int *offsets, const uint32_t *pairs,
                          int64_t cap, uint32_t nrec, const float bg[3], float *loss, unsigned long long *contrib,
-                         int *queue, cudaStream_t st) {
+                         int *queue, bool pdl, cudaStream_t st) {
     if (count)
-        launch_one<kMode, true, kStrip>(b, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, st);
+        launch_one<kMode, true, kStrip>(b, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, pdl, st);
     else
-        launch_one<kMode, false, kStrip>(b, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, st);
+        launch_one<kMode, false, kStrip>(b, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, pdl, st);
 }
 
 template <int kMode>
 static void launch_mode(const Batch &b, int strip, bool count, const float4 *rec, const int *offsets,
                         const uint32_t *pairs, int64_t cap, uint32_t nrec, const float bg[3], float *loss,
-                        unsigned long long *contrib, int *queue, cudaStream_t st) {
+                        unsigned long long *contrib, int *queue, bool pdl, cudaStream_t st) {
     if (strip == 4)
-        launch_strip<kMode, 4>(b, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, st);
+        launch_strip<kMode, 4>(b, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, pdl, st);
     else if (strip == 2)
-        launch_strip<kMode, 2>(b, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, st);
+        launch_strip<kMode, 2>(b, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, pdl, st);
     else
-        launch_strip<kMode, 1>(b, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, st);
+        launch_strip<kMode, 1>(b, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, pdl, st);
 }
 
 int launch_raster_fwd(const Batch &b, int mode, int strip, const float4 *rec, const int *offsets,
                       const uint32_t *pairs, int64_t cap, const float bg[3], float *loss, unsigned long long *contrib,
-                      int *queue, cudaStream_t st) {
+                      int *queue, bool pdl, cudaStream_t st) {
     if (b.total_tiles == 0) return 0;
     const uint32_t nrec = (uint32_t)((int64_t)b.n_views * b.n_list);
     const bool count = contrib != nullptr;
-    if (queue) cudaMemsetAsync(queue, 0, sizeof(int), st);
+    if (queue) {
+        cudaMemsetAsync(queue, 0, sizeof(int), st);
+        pdl = false;  // the operation just before the raster is this memset, not the scatter
+    }
     switch (mode) {
         case kRasterFused:
-            launch_mode<kRasterFused>(b, strip, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, st);
+            launch_mode<kRasterFused>(b, strip, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, pdl,
+                                      st);
             break;
         case kRasterAux:
-            launch_mode<kRasterAux>(b, strip, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, st);
+            launch_mode<kRasterAux>(b, strip, count, rec, offsets, pairs, cap, nrec, bg, loss, contrib, queue, pdl,
+                                    st);
             break;
         default:
             launch_mode<kRasterSums>(b, strip, false, rec, offsets, pairs, cap, nrec, bg, nullptr, nullptr, queue,
-                                     st);
+                                     pdl, st);
             break;
     }
     return 0;
