@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kChainThreads, 3) project_bwd_kernel(const __g
         *dst = v;
     }
     // dL/dsigma: the block's sum to sig_part, then the last block to finish sums the partials in
-    // block order (the same result on every run) and resets the counter for the next launch
+    // block order (no float atomics on one address) and resets the counter for the next launch
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) gsig_local += __shfl_xor_sync(0xffffffffu, gsig_local, off);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = gsig_local;

@@ -125,3 +125,28 @@ def test_backward_accumulate_sums_calls():
         want = sep[0][k] + sep[1][k]
         # float atomics sum in a different order in the two cases: rounding-level differences
         assert (acc[k] - want).abs().max().item() <= 1e-5 * max(1e-30, want.abs().max().item()), k
+
+
+def test_second_backward_of_one_forward():
+    """Two backward calls after one forward: the second zeroes the screen-space sums itself (the
+    forward's projection zeroed them for the first) and equals a fresh forward + backward."""
+    n = 8000
+    scene = scenes.unbounded_scene(n, 6200)
+    cam = scenes.random_camera(6203, 96, 72)
+    mask = scenes.random_active_mask(n, 0.3, 6202)
+    sp = SplatParams.from_numpy(scene)
+    r = Renderer(n, [(cam["width"], cam["height"])])
+    r.set_active(torch.as_tensor(mask, device="cuda"))
+    r.commit_frozen(sp, cam, 0, mode="recompute")
+    gs = [torch.as_tensor(np.random.default_rng(20 + k).normal(size=(72, 96, 3)), dtype=torch.float32,
+                          device="cuda") for k in range(2)]
+    r.forward(sp, [cam], [0])
+    first = {k: x.clone() for k, x in r.backward(sp, [gs[0]]).items()}
+    second = {k: x.clone() for k, x in r.backward(sp, [gs[1]]).items()}
+    r.forward(sp, [cam], [0])
+    fresh = r.backward(sp, [gs[1]])
+    for k in second:
+        # float atomics sum in a different order in the two runs: rounding-level differences
+        scale = max(1e-30, fresh[k].abs().max().item())
+        assert (second[k] - fresh[k]).abs().max().item() <= 1e-5 * scale, k
+        assert (first[k] - second[k]).abs().max().item() > 1e-3 * scale, k  # the two losses differ
