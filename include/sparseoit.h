@@ -248,7 +248,10 @@ int sparseoit_forward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const 
  * active splats' parameters (summed over its views).  d_grad_images: NULL
  * when that forward had targets (fused L1), else n_views device arrays
  * [H, W, 3] holding dL/dC in the forward's view order.  `splats` must be the
- * same parameter values as in the forward. */
+ * same parameter values as in the forward.  After a forward with targets (or
+ * sparseoit_loss_l1_dssim) the call may be repeated; after a forward without
+ * targets it turns that forward's planes into the backward state in place, so a
+ * second backward (or a loss) of the same forward returns SPARSEOIT_ERR_STATE. */
 int sparseoit_backward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const float *const *d_grad_images,
                        sparseoit_grads *out, void *stream);
 

@@ -98,6 +98,9 @@ struct sparseoit_ctx {
     // last forward
     bool have_fwd = false;
     bool last_fused = false;
+    // a backward after a forward without targets turned its (F, T, Q) planes into the backward
+    // state in place: another backward or loss needs a new forward
+    bool planes_consumed = false;
     Batch last_batch;
     int last_n_list = 0;
     const int *last_list = nullptr;  // index list of the last forward (active list or identity)
@@ -685,6 +688,7 @@ static int forward_impl(sparseoit_ctx *ctx, const sparseoit_splats *splats, cons
     ctx->sgrad_clean = true;
     ctx->have_fwd = true;
     ctx->last_fused = d_targets != nullptr;
+    ctx->planes_consumed = false;
     ctx->last_batch = b;
     ctx->last_list = list;
     ctx->last_n_list = (int)n_list;
@@ -717,6 +721,10 @@ int sparseoit_backward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const
     cudaStream_t st = (cudaStream_t)stream;
     Batch &b = ctx->last_batch;
     if (!ctx->last_fused) {
+        if (ctx->planes_consumed)
+            return fail(ctx, SPARSEOIT_ERR_STATE,
+                        "backward: an earlier backward of this forward (no targets) consumed its planes; run the "
+                        "forward again");
         if (!d_grad_images) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "grad images needed (forward had no targets)");
         for (int k = 0; k < b.n_views; ++k) {
             if (!d_grad_images[k]) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "grad image pointer is null");
@@ -725,6 +733,7 @@ int sparseoit_backward(sparseoit_ctx *ctx, const sparseoit_splats *splats, const
         ProfScope ps(ctx, "prep_state", st);
         launch_prep_state(b, splats->bg, st);
         CK_LAUNCH("prep_state_kernel");
+        ctx->planes_consumed = true;
     }
     const int64_t nrec = (int64_t)b.n_views * ctx->last_n_list;
     // the forward's projection zeroed the screen-space sums; a second backward of the same forward
@@ -874,7 +883,7 @@ int sparseoit_loss_l1_dssim(sparseoit_ctx *ctx, const float *const *d_targets, f
     if (!ctx) return SPARSEOIT_ERR_INVALID_ARG;
     if (!d_targets || !d_loss || !bg) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "loss: null argument");
     if (!(lambda >= 0.f && lambda <= 1.f)) return fail(ctx, SPARSEOIT_ERR_INVALID_ARG, "loss: lambda outside [0, 1]");
-    if (!ctx->have_fwd || ctx->last_generation != ctx->generation || ctx->last_fused)
+    if (!ctx->have_fwd || ctx->last_generation != ctx->generation || ctx->last_fused || ctx->planes_consumed)
         return fail(ctx, SPARSEOIT_ERR_STATE, "loss: needs the state of a forward run without targets");
     cudaStream_t st = (cudaStream_t)stream;
     Batch &b = ctx->last_batch;

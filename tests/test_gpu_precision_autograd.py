@@ -6,6 +6,7 @@ import torch
 
 import oracle
 from paper_2605_13855_gb300 import scenes
+from paper_2605_13855_gb300._lib import ERR_STATE, SparseOITError
 from paper_2605_13855_gb300.renderer import Renderer, SparseOITRender, SplatParams
 from tests.parity_util import AMB_BAND, AMB_PIX_MAX, GRAD_TOL, IMG_TOL, check_against_oracle, grad_errors, \
     image_error, oracle_grads, to_np
@@ -128,8 +129,10 @@ def test_backward_accumulate_sums_calls():
 
 
 def test_second_backward_of_one_forward():
-    """Two backward calls after one forward: the second zeroes the screen-space sums itself (the
-    forward's projection zeroed them for the first) and equals a fresh forward + backward."""
+    """A backward repeated after one forward with targets (fused L1) zeroes the screen-space sums
+    itself (the forward's projection zeroed them for the first) and equals the first and a fresh
+    forward + backward; after a forward without targets the first backward consumes the forward's
+    planes, and a second one is refused."""
     n = 8000
     scene = scenes.unbounded_scene(n, 6200)
     cam = scenes.random_camera(6203, 96, 72)
@@ -138,15 +141,20 @@ def test_second_backward_of_one_forward():
     r = Renderer(n, [(cam["width"], cam["height"])])
     r.set_active(torch.as_tensor(mask, device="cuda"))
     r.commit_frozen(sp, cam, 0, mode="recompute")
-    gs = [torch.as_tensor(np.random.default_rng(20 + k).normal(size=(72, 96, 3)), dtype=torch.float32,
-                          device="cuda") for k in range(2)]
-    r.forward(sp, [cam], [0])
-    first = {k: x.clone() for k, x in r.backward(sp, [gs[0]]).items()}
-    second = {k: x.clone() for k, x in r.backward(sp, [gs[1]]).items()}
-    r.forward(sp, [cam], [0])
-    fresh = r.backward(sp, [gs[1]])
+    target = torch.as_tensor(np.random.default_rng(21).uniform(size=(72, 96, 3)), dtype=torch.float32, device="cuda")
+    r.forward(sp, [cam], [0], targets=[target])
+    first = {k: x.clone() for k, x in r.backward(sp).items()}
+    second = {k: x.clone() for k, x in r.backward(sp).items()}
+    r.forward(sp, [cam], [0], targets=[target])
+    fresh = r.backward(sp)
     for k in second:
-        # float atomics sum in a different order in the two runs: rounding-level differences
+        # float atomics sum in a different order in the runs: rounding-level differences
         scale = max(1e-30, fresh[k].abs().max().item())
+        assert (second[k] - first[k]).abs().max().item() <= 1e-5 * scale, k
         assert (second[k] - fresh[k]).abs().max().item() <= 1e-5 * scale, k
-        assert (first[k] - second[k]).abs().max().item() > 1e-3 * scale, k  # the two losses differ
+    g = torch.as_tensor(np.random.default_rng(22).normal(size=(72, 96, 3)), dtype=torch.float32, device="cuda")
+    r.forward(sp, [cam], [0])
+    r.backward(sp, [g])
+    with pytest.raises(SparseOITError) as e:
+        r.backward(sp, [g])
+    assert e.value.code == ERR_STATE
