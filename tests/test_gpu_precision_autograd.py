@@ -158,3 +158,33 @@ def test_second_backward_of_one_forward():
     with pytest.raises(SparseOITError) as e:
         r.backward(sp, [g])
     assert e.value.code == ERR_STATE
+
+
+def test_backward_after_foreign_work_on_the_stream():
+    """The backward's kernels are programmatic dependents of the operation before them: with a torch
+    kernel and a device-to-host copy enqueued between the forward and the backward on the same
+    stream, the gradients equal those of the plain sequence."""
+    n = 8000
+    scene = scenes.unbounded_scene(n, 6300)
+    cam = scenes.random_camera(6303, 96, 72)
+    mask = scenes.random_active_mask(n, 0.3, 6302)
+    sp = SplatParams.from_numpy(scene)
+    r = Renderer(n, [(cam["width"], cam["height"])])
+    stream = torch.cuda.Stream()
+    target = torch.as_tensor(np.random.default_rng(31).uniform(size=(72, 96, 3)), dtype=torch.float32, device="cuda")
+    scratch = torch.zeros(1 << 22, device="cuda")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        r.set_active(torch.as_tensor(mask, device="cuda"), stream=stream)
+        r.commit_frozen(sp, cam, 0, mode="recompute", stream=stream)
+        _, loss = r.forward(sp, [cam], [0], targets=[target], stream=stream)
+        plain = {k: x.clone() for k, x in r.backward(sp, stream=stream).items()}
+        _, loss = r.forward(sp, [cam], [0], targets=[target], stream=stream)
+        scratch.mul_(2.0).add_(1.0)                       # a foreign kernel on the stream
+        host_loss = loss.to("cpu", non_blocking=True)     # and a copy to host memory
+        mixed = r.backward(sp, stream=stream)
+    stream.synchronize()
+    assert np.isfinite(host_loss.item())
+    for k in plain:
+        scale = max(1e-30, plain[k].abs().max().item())
+        assert (mixed[k] - plain[k]).abs().max().item() <= 1e-5 * scale, k
