@@ -282,7 +282,8 @@ typedef struct {
  * (2) the backward raster with the tile's splats sorted by first row or in
  * arena order, each as one block per tile and as persistent blocks.  Each
  * candidate: 1 warm-up + `reps` timed runs, CUDA events on `stream`.  The
- * fastest of each is kept for later calls.  The outputs of the last call are
+ * fastest of each is kept for later calls, a persistent raster only if it is
+ * at least 2 % faster than one block per tile.  The outputs of the last call are
  * valid forward outputs (a backward must follow it as after any forward).
  * Synchronises `stream`; not for use during stream capture. */
 int sparseoit_autotune(sparseoit_ctx *ctx, const sparseoit_splats *splats, const sparseoit_camera *cams,
